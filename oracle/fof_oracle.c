@@ -1,0 +1,683 @@
+/*
+ * fof_oracle.c -- plain, slow CPU oracle for the Friends-of-Friends hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path links, loads or calls
+ * this file: only the tests, the smoke check and the CPU-baseline leg of the
+ * benchmark use it.  It shares no code, header, table or constant with the CUDA
+ * library; each side implements the method from the paper independently.
+ *
+ * Build with  -O2 -ffp-contract=off  and no fast-math: every float operation
+ * below must be one IEEE binary32 operation, rounded once, so that the pair
+ * predicate is evaluated exactly as specified (no fused multiply-add).
+ *
+ * What it computes, and where the paper defines it (Horowitz & Bayer,
+ * "jFoF: GPU Cluster Finding with Gradient Propagation"):
+ *   - FoF groups: two particles are friends when their (periodic minimum-image)
+ *     separation is within the linking length b; groups are the connected
+ *     components of the friendship graph (Sec. 1; Sec. 2 steps (iv)-(v);
+ *     Algorithm 2 uses "<= b").  Raw label = smallest particle index in the
+ *     component, i.e. the fixed point of the min-label propagation of Sec. 2
+ *     step (v) and Algorithm 2.
+ *   - candidate search on a linked-cell grid over the periodic box, 27-cell
+ *     stencil with (. mod n) wrapping (Sec. 2.2, Algorithm 2); uncapped.
+ *   - compaction to 0..H-1 and per-group counts (Sec. 2 step (vi)), with a
+ *     minimum group size cut.
+ *   - halo properties: mass, periodic centre of mass, velocity mean and 1-D
+ *     velocity dispersion (Sec. 3.1, Eq. 4, Table 1 "halo position").
+ *   - frozen-assignment adjoint of those properties (Sec. 3.1, Eq. 4).
+ *   - REINFORCE topological mode: Bernoulli edges over a fixed candidate list
+ *     (Sec. 3.2, Eq. 8; neighbour list not rebuilt), per-sample FoF, and the
+ *     score-function gradient estimate with a baseline (Eqs. 6-7).
+ *
+ * Readings where the paper is silent (each one is also listed in the design
+ * notes of the repository):
+ *   - link iff d2 <= b2, d2 = (dx*dx + dy*dy) + dz*dz in binary32, with the
+ *     minimum-image correction applied per axis to dx = xj - xi:
+ *       if dx > L/2: dx -= L; else if dx < -L/2: dx += L.
+ *   - cell grid: n <= floor(L / (1.01 b)) cells per axis (the printed
+ *     n = ceil(L/b) gives cells smaller than b and misses links); n = 1 or
+ *     n >= 3; labels do not depend on n.
+ *   - optional wrap x' = x - L*floor(x/L), then x' >= L or x' < 0 -> 0.
+ *   - halo ids ascending by raw label; groups with count >= min_size kept.
+ *   - periodic COM about the group's smallest-index member r:
+ *       com = wrap(x_r + (1/n) sum_i mi(x_i - x_r)).
+ *   - velocity dispersion sigma^2 = (1/(3n)) sum_i |v_i - vbar|^2 (two-pass).
+ *   - REINFORCE edge probability p = 1/(1+E(-z)), z = (b-d)/tau (form 0) or
+ *     z = alpha (b2 - d2)/b2 (form 1, Eq. 8); candidates d2 < (1.5 b)^2 style
+ *     cut r_cut; E is the Cody-Waite + degree-7 Taylor exponential below;
+ *     uniforms from Philox4x32-10 (Salmon et al., SC'11) keyed by the seed with
+ *     counter (min index, max index, floor(k/4), 0), word k mod 4, top 24 bits.
+ *
+ * Parity pins (see tests/): brute force for small N, cubic lattices, chains
+ * across the periodic boundary, exact ties, invariants, closed-form halos,
+ * central finite differences, Philox known-answer vectors, exact enumeration
+ * of tiny REINFORCE graphs.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+/* ------------------------------------------------------------------------ */
+/* Status codes (own numbering; the oracle reports, it never aborts).        */
+#define ORC_OK 0
+#define ORC_EINVAL 1
+#define ORC_ERANGE 2
+#define ORC_ENOMEM 3
+
+/* ------------------------------------------------------------------------ */
+/* The pair predicate (Sec. 2 step (iv); Algorithm 2 minimum image).          */
+
+static float orc_min_image(float xj, float xi, float L, float hL)
+{
+    float d = xj - xi;
+    if (d > hL)
+        d = d - L;
+    else if (d < -hL)
+        d = d + L;
+    return d;
+}
+
+/* d2 between particles i and j (float positions, AoS [N,3]). */
+float orc_dist2(const float *pi, const float *pj, float L)
+{
+    float hL = 0.5f * L;
+    float dx = orc_min_image(pj[0], pi[0], L, hL);
+    float dy = orc_min_image(pj[1], pi[1], L, hL);
+    float dz = orc_min_image(pj[2], pi[2], L, hL);
+    float sx = dx * dx;
+    float sy = dy * dy;
+    float sz = dz * dz;
+    float s = sx + sy;
+    return s + sz;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Union-find with the smaller index as the root (sequential).               */
+
+static int32_t uf_find(int32_t *parent, int32_t x)
+{
+    int32_t r = x;
+    while (parent[r] != r)
+        r = parent[r];
+    while (parent[x] != r) { /* path compression */
+        int32_t nx = parent[x];
+        parent[x] = r;
+        x = nx;
+    }
+    return r;
+}
+
+static void uf_union(int32_t *parent, int32_t a, int32_t b)
+{
+    int32_t ra = uf_find(parent, a), rb = uf_find(parent, b);
+    if (ra == rb)
+        return;
+    if (ra < rb)
+        parent[rb] = ra;
+    else
+        parent[ra] = rb;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Input normalisation: optional periodic wrap (Algorithm 2 "X mod L").       */
+
+int orc_wrap(float *pos, int64_t N, float L)
+{
+    for (int64_t i = 0; i < 3 * N; ++i) {
+        float x = pos[i];
+        float q = floorf(x / L);
+        float w = x - L * q;
+        if (w >= L)
+            w = 0.0f;
+        if (w < 0.0f)
+            w = 0.0f;
+        pos[i] = w;
+    }
+    return ORC_OK;
+}
+
+/* Largest legal cells-per-axis for the grid: floor(L / (1.01 b)); n = 2 is
+   replaced by 1 so that the 27-cell stencil never visits a cell twice. */
+int32_t orc_max_cells_per_axis(float L, float b)
+{
+    double m = floor((double)L / (1.01 * (double)b));
+    if (m < 1.0)
+        m = 1.0;
+    if (m > 2048.0)
+        m = 2048.0;
+    int32_t n = (int32_t)m;
+    if (n == 2)
+        n = 1;
+    return n;
+}
+
+static int32_t cell_coord(float x, float inv_cell, int32_t n)
+{
+    float u = x * inv_cell;
+    int32_t c = (int32_t)floorf(u);
+    if (c > n - 1)
+        c = n - 1;
+    if (c < 0)
+        c = 0;
+    return c;
+}
+
+/* ------------------------------------------------------------------------ */
+/* FoF labels via a linked-cell grid + union-find (Sec. 2.2, Algorithm 2).    */
+/* label[i] = smallest index in i's component.  n_axis = 0 picks the largest  */
+/* legal grid capped so that n^3 <= 8 N.  Returns ORC_* status.               */
+
+int orc_fof_labels(const float *pos, int64_t N, float L, float b, int32_t n_axis,
+                   int32_t *label)
+{
+    if (N < 1 || !(L > 0.0f) || !(b > 0.0f) || !(b < 0.5f * L))
+        return ORC_EINVAL;
+    for (int64_t i = 0; i < 3 * N; ++i)
+        if (!(pos[i] >= 0.0f && pos[i] < L))
+            return ORC_ERANGE;
+    int32_t nmax = orc_max_cells_per_axis(L, b);
+    int32_t n = n_axis;
+    if (n <= 0) {
+        n = nmax;
+        while (n > 3 && (double)n * n * n > 8.0 * (double)N)
+            --n;
+    }
+    if (n > nmax || n == 2)
+        return ORC_EINVAL;
+    int64_t ncell = (int64_t)n * n * n;
+    float inv_cell = (float)((double)n / (double)L);
+
+    int64_t *head = (int64_t *)malloc(sizeof(int64_t) * ncell);
+    int64_t *next = (int64_t *)malloc(sizeof(int64_t) * N);
+    int32_t *parent = label; /* union-find forest lives in the output */
+    if (!head || !next) {
+        free(head);
+        free(next);
+        return ORC_ENOMEM;
+    }
+    for (int64_t c = 0; c < ncell; ++c)
+        head[c] = -1;
+    /* linked list per cell, built in descending index so that each list is
+       ascending in particle index */
+    for (int64_t i = N - 1; i >= 0; --i) {
+        int32_t ix = cell_coord(pos[3 * i + 0], inv_cell, n);
+        int32_t iy = cell_coord(pos[3 * i + 1], inv_cell, n);
+        int32_t iz = cell_coord(pos[3 * i + 2], inv_cell, n);
+        int64_t c = ix + (int64_t)n * (iy + (int64_t)n * iz);
+        next[i] = head[c];
+        head[c] = i;
+    }
+    for (int64_t i = 0; i < N; ++i)
+        parent[i] = (int32_t)i;
+
+    float b2 = b * b;
+    for (int64_t i = 0; i < N; ++i) {
+        int32_t ix = cell_coord(pos[3 * i + 0], inv_cell, n);
+        int32_t iy = cell_coord(pos[3 * i + 1], inv_cell, n);
+        int32_t iz = cell_coord(pos[3 * i + 2], inv_cell, n);
+        /* the 27 neighbour cells with (. mod n) wrapping; duplicates removed
+           (only possible for n == 1) */
+        int64_t seen[27];
+        int nseen = 0;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int32_t cx = ((ix + dx) % n + n) % n;
+                    int32_t cy = ((iy + dy) % n + n) % n;
+                    int32_t cz = ((iz + dz) % n + n) % n;
+                    int64_t c = cx + (int64_t)n * (cy + (int64_t)n * cz);
+                    int dup = 0;
+                    for (int s = 0; s < nseen; ++s)
+                        if (seen[s] == c)
+                            dup = 1;
+                    if (dup)
+                        continue;
+                    seen[nseen++] = c;
+                    for (int64_t j = head[c]; j >= 0; j = next[j]) {
+                        if (j <= i)
+                            continue; /* each unordered pair once */
+                        if (orc_dist2(pos + 3 * i, pos + 3 * j, L) <= b2)
+                            uf_union(parent, (int32_t)i, (int32_t)j);
+                    }
+                }
+    }
+    for (int64_t i = 0; i < N; ++i)
+        label[i] = uf_find(parent, (int32_t)i);
+    free(head);
+    free(next);
+    return ORC_OK;
+}
+
+/* O(N^2) brute force over all pairs with the same predicate (pin for the
+   cell-list oracle, Sec. 2: "the naive cost of pairwise searches"). */
+int orc_fof_brute(const float *pos, int64_t N, float L, float b, int32_t *label)
+{
+    if (N < 1 || !(b > 0.0f) || !(b < 0.5f * L))
+        return ORC_EINVAL;
+    float b2 = b * b;
+    for (int64_t i = 0; i < N; ++i)
+        label[i] = (int32_t)i;
+    for (int64_t i = 0; i < N; ++i)
+        for (int64_t j = i + 1; j < N; ++j)
+            if (orc_dist2(pos + 3 * i, pos + 3 * j, L) <= b2)
+                uf_union(label, (int32_t)i, (int32_t)j);
+    for (int64_t i = 0; i < N; ++i)
+        label[i] = uf_find(label, (int32_t)i);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Compaction + histogram + minimum-size cut (Sec. 2 step (vi); Alg. 1-2     */
+/* "Compaction").  halo_id ascending by raw label; -1 below the cut.         */
+/* count has room for N entries.  Returns H (>= 0) or -1 on bad input.       */
+
+int64_t orc_groups(const int32_t *label, int64_t N, int32_t min_size,
+                   int32_t *halo_id, int32_t *count)
+{
+    if (N < 1 || min_size < 1)
+        return -1;
+    int64_t *cnt = (int64_t *)calloc((size_t)N, sizeof(int64_t));
+    int64_t *hid = (int64_t *)malloc(sizeof(int64_t) * N);
+    if (!cnt || !hid) {
+        free(cnt);
+        free(hid);
+        return -1;
+    }
+    for (int64_t i = 0; i < N; ++i) {
+        if (label[i] < 0 || label[i] >= N) {
+            free(cnt);
+            free(hid);
+            return -1;
+        }
+        cnt[label[i]] += 1;
+    }
+    int64_t H = 0;
+    for (int64_t r = 0; r < N; ++r) {
+        hid[r] = -1;
+        if (label[r] == r && cnt[r] >= min_size) {
+            hid[r] = H;
+            count[H] = (int32_t)cnt[r];
+            ++H;
+        }
+    }
+    for (int64_t i = 0; i < N; ++i)
+        halo_id[i] = (int32_t)hid[label[i]];
+    free(cnt);
+    free(hid);
+    return H;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Halo properties in FP64 (Sec. 3.1, Eq. 4; Table 1).                       */
+/* pos, vel: [N,3] doubles (float inputs widen exactly).  Outputs [H] / [H,3].*/
+
+static double wrap_f64(double c, double L)
+{
+    double w = c - L * floor(c / L);
+    if (w >= L || w < 0.0)
+        w = 0.0;
+    return w;
+}
+
+static double mi_f64(double d, double L)
+{
+    if (d > 0.5 * L)
+        d -= L;
+    else if (d < -0.5 * L)
+        d += L;
+    return d;
+}
+
+int orc_halo_props(const double *pos, const double *vel, const int32_t *halo_id,
+                   int64_t N, int64_t H, double L, double particle_mass,
+                   double *mass, double *com, double *vmean, double *sigv)
+{
+    if (H < 0)
+        return ORC_EINVAL;
+    int64_t *n = (int64_t *)calloc((size_t)(H > 0 ? H : 1), sizeof(int64_t));
+    int64_t *ref = (int64_t *)malloc(sizeof(int64_t) * (size_t)(H > 0 ? H : 1));
+    double *sx = (double *)calloc((size_t)(H > 0 ? 3 * H : 1), sizeof(double));
+    double *sv = (double *)calloc((size_t)(H > 0 ? 3 * H : 1), sizeof(double));
+    double *s2 = (double *)calloc((size_t)(H > 0 ? H : 1), sizeof(double));
+    if (!n || !ref || !sx || !sv || !s2) {
+        free(n); free(ref); free(sx); free(sv); free(s2);
+        return ORC_ENOMEM;
+    }
+    for (int64_t h = 0; h < H; ++h)
+        ref[h] = -1;
+    /* pass 1: reference member (smallest index), counts, sums */
+    for (int64_t i = 0; i < N; ++i) {
+        int32_t h = halo_id[i];
+        if (h < 0)
+            continue;
+        if (ref[h] < 0)
+            ref[h] = i;
+        n[h] += 1;
+    }
+    for (int64_t i = 0; i < N; ++i) {
+        int32_t h = halo_id[i];
+        if (h < 0)
+            continue;
+        for (int a = 0; a < 3; ++a) {
+            sx[3 * h + a] += mi_f64(pos[3 * i + a] - pos[3 * ref[h] + a], L);
+            sv[3 * h + a] += vel[3 * i + a];
+        }
+    }
+    for (int64_t h = 0; h < H; ++h) {
+        double nh = (double)n[h];
+        mass[h] = particle_mass * nh;
+        for (int a = 0; a < 3; ++a) {
+            com[3 * h + a] = wrap_f64(pos[3 * ref[h] + a] + sx[3 * h + a] / nh, L);
+            vmean[3 * h + a] = sv[3 * h + a] / nh;
+        }
+    }
+    /* pass 2: dispersion about the mean */
+    for (int64_t i = 0; i < N; ++i) {
+        int32_t h = halo_id[i];
+        if (h < 0)
+            continue;
+        for (int a = 0; a < 3; ++a) {
+            double d = vel[3 * i + a] - vmean[3 * h + a];
+            s2[h] += d * d;
+        }
+    }
+    for (int64_t h = 0; h < H; ++h)
+        sigv[h] = sqrt(s2[h] / (3.0 * (double)n[h]));
+    free(n); free(ref); free(sx); free(sv); free(s2);
+    return ORC_OK;
+}
+
+/* Frozen-assignment adjoint (Sec. 3.1, Eq. 4): memberships fixed, so
+     d com_h / d x_i   = I / n_h             (every member, reference included)
+     d vbar_h / d v_i  = I / n_h
+     d sigma_h / d v_i = (v_i - vbar_h) / (3 n_h sigma_h), 0 when sigma_h = 0.
+   g_com, g_vmean: [H,3] or NULL; g_sigv: [H] or NULL.  Outputs [N,3]. */
+int orc_halo_props_backward(const double *vel, const int32_t *halo_id, int64_t N,
+                            int64_t H, const double *vmean, const double *sigv,
+                            const double *g_com, const double *g_vmean,
+                            const double *g_sigv, double *g_pos, double *g_vel)
+{
+    int64_t *n = (int64_t *)calloc((size_t)(H > 0 ? H : 1), sizeof(int64_t));
+    if (!n)
+        return ORC_ENOMEM;
+    for (int64_t i = 0; i < N; ++i)
+        if (halo_id[i] >= 0)
+            n[halo_id[i]] += 1;
+    for (int64_t i = 0; i < N; ++i) {
+        int32_t h = halo_id[i];
+        for (int a = 0; a < 3; ++a) {
+            g_pos[3 * i + a] = 0.0;
+            g_vel[3 * i + a] = 0.0;
+        }
+        if (h < 0)
+            continue;
+        double nh = (double)n[h];
+        for (int a = 0; a < 3; ++a) {
+            if (g_com)
+                g_pos[3 * i + a] = g_com[3 * h + a] / nh;
+            double gv = 0.0;
+            if (g_vmean)
+                gv += g_vmean[3 * h + a] / nh;
+            if (g_sigv && sigv[h] > 0.0)
+                gv += g_sigv[h] * (vel[3 * i + a] - vmean[3 * h + a]) / (3.0 * nh * sigv[h]);
+            g_vel[3 * i + a] = gv;
+        }
+    }
+    free(n);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Counter-based generator: Philox4x32-10 (Salmon, Moraes, Dror & Shaw,      */
+/* "Parallel random numbers: as easy as 1, 2, 3", SC'11).  Round function:   */
+/* two 32x32->64 multiplies by M0, M1, xor with the key, word shuffle; key   */
+/* bumped by the Weyl constants between rounds.                              */
+
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += W0;
+        k1 += W1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Uniform in [0,1) for edge (i,j) and sample k: 24 top bits of one Philox
+   word, exactly representable in binary32. */
+float orc_edge_uniform(uint64_t seed, int32_t i, int32_t j, int32_t k)
+{
+    uint32_t lo = (uint32_t)(i < j ? i : j), hi = (uint32_t)(i < j ? j : i);
+    uint32_t ctr[4] = {lo, hi, (uint32_t)k >> 2, 0u};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    uint32_t w = out[k & 3];
+    return (float)(w >> 8) * (1.0f / 16777216.0f);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Deterministic binary32 exponential: Cody-Waite range reduction            */
+/* x = k ln2 + r with ln2 split into a binary32 head and tail, then the      */
+/* degree-7 Taylor polynomial sum_{m<=7} r^m/m! by Horner with fused         */
+/* multiply-add (correctly rounded fmaf), then scaling by 2^k through the    */
+/* exponent field.  Input clamped to [-87, 87].  Constants are computed here */
+/* from their mathematical definitions in FP64 and rounded once.            */
+
+float orc_exp(float x)
+{
+    const float l2e = (float)(1.0 / M_LN2);
+    const float ln2_hi = (float)M_LN2;
+    const float ln2_lo = (float)(M_LN2 - (double)ln2_hi);
+    float c[8];
+    double f = 1.0;
+    for (int m = 0; m < 8; ++m) {
+        if (m > 0)
+            f *= (double)m;
+        c[m] = (float)(1.0 / f);
+    }
+    if (x > 87.0f)
+        x = 87.0f;
+    if (x < -87.0f)
+        x = -87.0f;
+    if (x != x)
+        x = 0.0f;
+    float t = x * l2e;
+    float k = rintf(t);
+    float r = fmaf(-k, ln2_hi, x);
+    r = fmaf(-k, ln2_lo, r);
+    float p = c[7];
+    for (int m = 6; m >= 0; --m)
+        p = fmaf(p, r, c[m]);
+    int32_t ki = (int32_t)k;
+    uint32_t bits = (uint32_t)(ki + 127) << 23;
+    float scale;
+    memcpy(&scale, &bits, sizeof(scale));
+    return p * scale;
+}
+
+/* Edge probability (Eq. 8 and the distance-sigmoid form). */
+float orc_edge_prob(float d, float d2, float b, float b2, int32_t form, float coef)
+{
+    float z;
+    if (form == 0)
+        z = (b - d) * coef; /* coef = 1/tau */
+    else
+        z = (b2 - d2) * coef; /* coef = alpha / b2 */
+    float e = orc_exp(-z);
+    return 1.0f / (1.0f + e);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Candidate pair list for REINFORCE (fixed, "do not rebuild the neighbor    */
+/* list", Sec. 3.2): unordered pairs i<j with d2 < rc2, sorted by (i, j),     */
+/* with d = sqrtf(d2) and the edge probability.  Returns the number of pairs; */
+/* writes at most cap of them.  Negative on bad input.                       */
+
+static int cmp_i32(const void *a, const void *b)
+{
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+int64_t orc_pairs(const float *pos, int64_t N, float L, float b, float r_cut,
+                  int32_t form, float coef, int64_t cap, int32_t *pi, int32_t *pj,
+                  float *pd, float *pp)
+{
+    if (N < 1 || !(r_cut > 0.0f) || !(r_cut < 0.5f * L))
+        return -1;
+    float rc2 = r_cut * r_cut;
+    float b2 = b * b;
+    int32_t n = orc_max_cells_per_axis(L, r_cut);
+    while (n > 3 && (double)n * n * n > 8.0 * (double)N)
+        --n;
+    int64_t ncell = (int64_t)n * n * n;
+    float inv_cell = (float)((double)n / (double)L);
+    int64_t *head = (int64_t *)malloc(sizeof(int64_t) * ncell);
+    int64_t *next = (int64_t *)malloc(sizeof(int64_t) * N);
+    int32_t *buf = (int32_t *)malloc(sizeof(int32_t) * N);
+    if (!head || !next || !buf) {
+        free(head); free(next); free(buf);
+        return -1;
+    }
+    for (int64_t c = 0; c < ncell; ++c)
+        head[c] = -1;
+    for (int64_t i = N - 1; i >= 0; --i) {
+        int32_t ix = cell_coord(pos[3 * i + 0], inv_cell, n);
+        int32_t iy = cell_coord(pos[3 * i + 1], inv_cell, n);
+        int32_t iz = cell_coord(pos[3 * i + 2], inv_cell, n);
+        int64_t c = ix + (int64_t)n * (iy + (int64_t)n * iz);
+        next[i] = head[c];
+        head[c] = i;
+    }
+    int64_t E = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        int32_t ix = cell_coord(pos[3 * i + 0], inv_cell, n);
+        int32_t iy = cell_coord(pos[3 * i + 1], inv_cell, n);
+        int32_t iz = cell_coord(pos[3 * i + 2], inv_cell, n);
+        int64_t seen[27];
+        int nseen = 0, nb = 0;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int32_t cx = ((ix + dx) % n + n) % n;
+                    int32_t cy = ((iy + dy) % n + n) % n;
+                    int32_t cz = ((iz + dz) % n + n) % n;
+                    int64_t c = cx + (int64_t)n * (cy + (int64_t)n * cz);
+                    int dup = 0;
+                    for (int s = 0; s < nseen; ++s)
+                        if (seen[s] == c)
+                            dup = 1;
+                    if (dup)
+                        continue;
+                    seen[nseen++] = c;
+                    for (int64_t j = head[c]; j >= 0; j = next[j])
+                        if (j > i && orc_dist2(pos + 3 * i, pos + 3 * j, L) < rc2)
+                            buf[nb++] = (int32_t)j;
+                }
+        qsort(buf, (size_t)nb, sizeof(int32_t), cmp_i32);
+        for (int s = 0; s < nb; ++s) {
+            if (E < cap) {
+                int32_t j = buf[s];
+                float d2 = orc_dist2(pos + 3 * i, pos + 3 * j, L);
+                float d = sqrtf(d2);
+                pi[E] = (int32_t)i;
+                pj[E] = j;
+                pd[E] = d;
+                pp[E] = orc_edge_prob(d, d2, b, b2, form, coef);
+            }
+            ++E;
+        }
+    }
+    free(head); free(next); free(buf);
+    return E;
+}
+
+/* Per-sample FoF over the sampled edges (Sec. 3.2, Eq. 8): edge e is present
+   in sample k iff u(seed, i_e, j_e, k) < p_e.  labels: [K,N] smallest index
+   per component; n_halos[k] = number of components with >= min_size members. */
+int orc_reinforce_sample(int64_t N, int64_t E, const int32_t *pi, const int32_t *pj,
+                         const float *pp, int32_t K, uint64_t seed, int32_t min_size,
+                         int32_t *labels, int32_t *n_halos)
+{
+    int64_t *cnt = (int64_t *)malloc(sizeof(int64_t) * N);
+    if (!cnt)
+        return ORC_ENOMEM;
+    for (int32_t k = 0; k < K; ++k) {
+        int32_t *lab = labels + (int64_t)k * N;
+        for (int64_t i = 0; i < N; ++i)
+            lab[i] = (int32_t)i;
+        for (int64_t e = 0; e < E; ++e)
+            if (orc_edge_uniform(seed, pi[e], pj[e], k) < pp[e])
+                uf_union(lab, pi[e], pj[e]);
+        for (int64_t i = 0; i < N; ++i) {
+            lab[i] = uf_find(lab, (int32_t)i);
+            cnt[i] = 0;
+        }
+        for (int64_t i = 0; i < N; ++i)
+            cnt[lab[i]] += 1;
+        int32_t h = 0;
+        for (int64_t i = 0; i < N; ++i)
+            if (lab[i] == i && cnt[i] >= min_size)
+                ++h;
+        n_halos[k] = h;
+    }
+    free(cnt);
+    return ORC_OK;
+}
+
+/* Score-function gradient (Eqs. 6-7) with respect to positions, FP64:
+     log p(y) = sum_e [y_e log p_e + (1-y_e) log(1-p_e)],
+     d log p(y) / d z_e = y_e - p_e,
+     form 0: z_e = (b - d_e)/tau     -> dz/dx_i = (x_j - x_i)_mi / (tau d_e)
+     form 1: z_e = alpha (b2-d2)/b2  -> dz/dx_i = 2 (alpha/b2) (x_j - x_i)_mi
+   and dz/dx_j = -dz/dx_i.  g = (1/K) sum_k A_k d log p(y_k) / dx.
+   coef is 1/tau (form 0) or alpha/b2 (form 1).  d_e = 0 contributes 0. */
+int orc_reinforce_grad(const float *pos, int64_t N, float L, int64_t E,
+                       const int32_t *pi, const int32_t *pj, const float *pp,
+                       int32_t K, uint64_t seed, const double *adv, int32_t form,
+                       double coef, double *g)
+{
+    for (int64_t i = 0; i < 3 * N; ++i)
+        g[i] = 0.0;
+    for (int64_t e = 0; e < E; ++e) {
+        int32_t i = pi[e], j = pj[e];
+        double s = 0.0;
+        for (int32_t k = 0; k < K; ++k) {
+            double y = orc_edge_uniform(seed, i, j, k) < pp[e] ? 1.0 : 0.0;
+            s += adv[k] * (y - (double)pp[e]);
+        }
+        s /= (double)K;
+        double dx[3], d2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            dx[a] = mi_f64((double)pos[3 * j + a] - (double)pos[3 * i + a], (double)L);
+            d2 += dx[a] * dx[a];
+        }
+        double fac;
+        if (form == 0) {
+            double d = sqrt(d2);
+            fac = d > 0.0 ? coef / d : 0.0;
+        } else {
+            fac = 2.0 * coef;
+        }
+        for (int a = 0; a < 3; ++a) {
+            g[3 * i + a] += s * fac * dx[a];
+            g[3 * j + a] -= s * fac * dx[a];
+        }
+    }
+    (void)N;
+    return ORC_OK;
+}
