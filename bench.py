@@ -1,0 +1,327 @@
+#!/usr/bin/env python
+"""Benchmark: FoF particles/s on the 1024^3 clustered box (labels bit-exact
+path: bin, sort, neighbour scan + union-find, labels, groups, halo properties).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one pass of the whole hot path over the box: jfof_fof (wrap/bin,
+two-level cell sort, 27-cell scan fused with union-find, raw labels, groups
+with the 20-particle cut and CSR members) followed by jfof_halo_props (mass,
+periodic COM, velocity mean and dispersion).  Inputs (12 GiB positions +
+12 GiB velocities) are resident in HBM when the timed region starts and are
+larger than L2, so no flush is needed between steps.
+
+Under torchrun (N > 1) every rank processes its own independent box (a
+replica with its own seed): the work shards with no collective on the data
+path (weak scaling).  Rank 0 prints one JSON line.
+
+--impl reference times the plain CPU oracle on a bounded sample of the same
+workload (a 128^3 box at the same density, linking length and halo
+statistics), on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import torch  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "FoF particles/s at 1024^3 (labels bit-exact) and % HBM peak; batched & bwd"
+UNIT = "particles/s"
+
+# Algorithmic bytes each kernel must move, per particle (link path) or per
+# halo member (groups/props); the roofline of the dominant kernel divides
+# these by its measured launch time.
+ALGO_BYTES = {
+    "bin_count": (12, "N"),          # read pos
+    "bin_scatter": (28, "N"),        # read pos 12, write float4 16
+    "brick_sort": (32, "N"),         # read float4 16, write float4 16 (+ cell table, added below)
+    "link_init": (4, "N"),
+    "link": (24, "N"),               # read sorted float4 16, parent read+write 8
+    "finalize_roots": (16, "N"),     # index 4, parent r/w 8, root minimum 4
+    "finalize_labels": (16, "N"),    # index 4, parent 4, root minimum 4, label write 4
+    "group_count": (12, "N"),        # label 4, count read+write 8
+    "group_assign": (16, "N"),       # label 4, two scan entries 8, halo id 4
+    "members_fill": (8, "N"),        # halo id 4, member write 4
+    "members_sort": (8, "M"),        # member read+write
+    "halo_props": (28, "M"),         # member 4, pos 12, vel 12
+}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.dev)], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        mx = max(r[1] for r in rows)
+        load = [r[0] for r in rows if r[0] > 0.5 * mx] or [r[0] for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[2][k].lower() == "active"})
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_sample_spec():
+    """The 1024^3 workload at 1/512 of its volume: a 128^3 box with the same
+    density (L = 125), linking length 0.1953125 and halo statistics
+    (5M * 2^21 / 2^30 halos holding 55%)."""
+    full = synth.BOX_1024
+    N = 128 ** 3
+    nh = int(round(full.n_halos * N / full.N))
+    return synth.BoxSpec("fof_128cubed_L125_sample", N, full.L / 8, full.b, nh, full.frac, 0)
+
+
+def time_oracle(spec, reps=1):
+    import numpy as np
+
+    import oracle
+    pos, vel = synth.generate(spec, device="cpu")
+    pos_np = pos.numpy()
+    vel64 = vel.numpy().astype(np.float64)
+    pos64 = pos_np.astype(np.float64)
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        lab = oracle.fof_labels(pos_np, spec.L, spec.b)
+        hid, cnt = oracle.groups(lab, spec.min_size)
+        oracle.halo_props(pos64, vel64, hid, len(cnt), spec.L)
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    spec = cpu_sample_spec()
+    oracle_mod = __import__("oracle")
+    oracle_mod.build()
+    for _ in range(args.warmup):
+        time_oracle(spec)
+    ts = [time_oracle(spec)[0] for _ in range(args.steps)]
+    t = sum(ts)
+    value = spec.N * args.steps / t
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": spec.name, "N": spec.N, "L": spec.L, "b": spec.b,
+                   "min_size": spec.min_size, "note": "CPU oracle on a bounded sample of the 1024^3 workload"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{spec.name}: 128^3 particles, labels+groups+props, single thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="1024", choices=["1024", "256"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import paper_2510_26851_gb300 as J
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    spec = synth.BOX_1024 if args.workload == "1024" else synth.BOX_256
+    if world > 1:
+        spec = synth.BoxSpec(spec.name, spec.N, spec.L, spec.b, spec.n_halos, spec.frac, spec.seed + rank)
+    pos, vel = synth.generate(spec, device="cuda")
+    torch.cuda.synchronize()
+    N = spec.N
+    n_axis = J.default_cells_per_axis(N, spec.L, spec.b)
+    ws = torch.empty(J.fof_all_bytes(N, n_axis), dtype=torch.uint8, device="cuda")
+    res = J.fof(pos, spec.L, spec.b, spec.min_size, n_axis=n_axis, workspace=ws)
+    props = J.halo_props(pos, vel, spec.L, res.groups)
+    J.sync()
+
+    def step():
+        J.fof(pos, spec.L, spec.b, spec.min_size, n_axis=n_axis, workspace=ws, out=res)
+        J.halo_props(pos, vel, spec.L, res.groups, out=props)
+
+    for _ in range(args.warmup):
+        step()
+    J.sync()
+    H = res.groups.n_halos
+    M = int(res.groups.halo_start[H].item())
+
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    J.trace_enable(True)
+    J.trace_read()  # drop warm-up records
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    trace = J.trace_read()
+    J.trace_enable(False)
+    J.sync()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    ms_per_step = ms / args.steps
+    value = world * N / (ms_per_step * 1e-3)
+
+    # roofline of the dominant kernel (largest total time in the timed region)
+    peak, peak_kind = load_peaks()
+    dom = max(trace.items(), key=lambda kv: kv[1][1])
+    name, (launches, tot_ms) = dom
+    per_launch_ms = tot_ms / launches
+    bpu, unit = ALGO_BYTES.get(name, (0, "N"))
+    units = N if unit == "N" else M
+    algo_bytes = bpu * units
+    if name == "brick_sort":
+        nb = -(-n_axis // 16)
+        algo_bytes += 4 * nb ** 3 * 4096
+    achieved = algo_bytes / (per_launch_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": algo_bytes, "launch_ms": per_launch_ms}
+    kernels = {k: {"launches": c, "ms_per_step": t / args.steps} for k, (c, t) in trace.items()}
+
+    # end to end through the public API: pinned host inputs -> device, the
+    # step, and the halo catalogue back to the host, all inside the timed region
+    e2e = None
+    if rank == 0 or world > 1:
+        hpos = torch.empty_like(pos, device="cpu").pin_memory()
+        hvel = torch.empty_like(vel, device="cpu").pin_memory()
+        hpos.copy_(pos)
+        hvel.copy_(vel)
+        dpos, dvel = pos, vel  # reuse the device buffers as copy targets
+        Hc = res.groups.H_cap
+        hcat = torch.empty(Hc, 9, dtype=torch.float32).pin_memory()
+        n_e2e = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d2h = 0
+        for _ in range(n_e2e):
+            dpos.copy_(hpos, non_blocking=True)
+            dvel.copy_(hvel, non_blocking=True)
+            step()
+            J.sync()
+            h = res.groups.n_halos
+            cat = torch.cat([res.groups.count[:h, None].float(), props.mass[:h, None], props.com[:h],
+                             props.vmean[:h], props.sigv[:h, None]], 1)
+            hcat[:h].copy_(cat, non_blocking=True)
+            torch.cuda.synchronize()
+            d2h = 4 + h * 9 * 4
+        e2e_s = (time.perf_counter() - t0) / n_e2e
+        e2e = {"value": world * N / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * N * 12,
+               "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            spec_s = cpu_sample_spec()
+            __import__("oracle").build()
+            ts = time_oracle(spec_s, reps=3)
+            t = sum(ts)
+            cpu = {"value": 3 * spec_s.N / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"{spec_s.name}: 128^3-particle box at the 1024^3 box's density, b and halo "
+                             f"statistics; labels + groups + props, single thread, 3 runs, {t:.1f} s"}
+        except Exception as e:  # the oracle is a reported baseline, never the product
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+
+    if rank == 0:
+        launches = sum(c for c, _ in trace.values()) // args.steps
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": spec.name, "N": N, "L": spec.L, "b": spec.b, "min_size": spec.min_size,
+                       "n_axis": n_axis, "n_halos": H, "members": M,
+                       "l2": "inputs (24 GiB) larger than L2; no flush",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "gpu_launches": launches * args.steps, "kernels": kernels,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,199 @@
+/*
+ * jfof.h -- C ABI of the GB300 (sm_103a) Friends-of-Friends hot path.
+ *
+ * The operations follow Horowitz & Bayer, "jFoF: GPU Cluster Finding with
+ * Gradient Propagation" (arXiv 2510.26851):
+ *   - input normalisation and labels (Sec. 2 steps (i), (v)),
+ *   - linked-cell candidate search over a periodic box (Sec. 2.2, Algorithm 2),
+ *   - the linking criterion d <= b on minimum-image separations (Sec. 2 step
+ *     (iv); Algorithm 2),
+ *   - connected components as labels = smallest member index (the fixed point
+ *     of the min-label propagation of Sec. 2 step (v) / Algorithm 2),
+ *   - compaction to halo ids and per-halo counts (Sec. 2 step (vi)),
+ *   - halo properties and their frozen-assignment adjoint (Sec. 3.1, Eq. 4,
+ *     Table 1),
+ *   - the REINFORCE topological mode (Sec. 3.2, Eqs. 6-8).
+ *
+ * Conventions shared by every call:
+ *   - Every array argument is a DEVICE pointer owned by the caller, unless the
+ *     argument's comment says "host".  The library never frees caller memory.
+ *   - Scratch memory is passed in by the caller as (ws, ws_bytes); the matching
+ *     *_bytes query gives the size.  No call allocates device memory except
+ *     jfof_create (a few bytes of status words per context).
+ *   - Work is enqueued on the context's CUDA stream and the call returns without
+ *     waiting, except where a comment says the call synchronises.
+ *   - Particle indices are int32: N <= 2^31 - 1.  Positions are float32 AoS
+ *     [N,3] in [0, L) unless JFOF_WRAP is given.
+ *   - Return value: JFOF_OK or an error code.  Argument errors are detected on
+ *     the host and nothing is enqueued.  Errors found by a kernel (a position
+ *     outside the box, a bounded wait that ran out, an overflowed capacity) are
+ *     latched in the context's device status word and returned by the next
+ *     jfof_sync() (which also clears it).  A kernel that latches an error still
+ *     keeps every memory access in bounds; its outputs are then unspecified.
+ */
+#ifndef JFOF_H
+#define JFOF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define JFOF_OK 0
+#define JFOF_EINVAL 1    /* bad argument (null pointer, N < 1, b <= 0, b >= L/2, ...) */
+#define JFOF_ERANGE 2    /* a position outside [0, L) without JFOF_WRAP, or not finite */
+#define JFOF_ENOMEM 3    /* workspace smaller than the *_bytes query */
+#define JFOF_ECUDA 4     /* a CUDA runtime call failed */
+#define JFOF_ETIMEOUT 5  /* a bounded device loop ran out of iterations */
+#define JFOF_EOVERFLOW 6 /* an output capacity was too small */
+
+/* Flags. */
+#define JFOF_WRAP 1u /* wrap positions into [0, L): x - L*floor(x/L), then >= L or < 0 -> 0
+                        (Algorithm 2 "X mod L") */
+
+typedef struct jfof_ctx jfof_ctx;
+
+/* Create a context on CUDA device `device` that enqueues on `stream` (a
+   cudaStream_t; NULL = the legacy default stream).  Allocates the context's
+   device status word.  *ctx receives the handle. */
+int jfof_create(jfof_ctx **ctx, int device, void *stream);
+
+/* Destroy a context (synchronises its stream first). */
+int jfof_destroy(jfof_ctx *ctx);
+
+/* Change the stream later calls enqueue on. */
+int jfof_set_stream(jfof_ctx *ctx, void *stream);
+
+/* Synchronise the context's stream, then return and clear the latched device
+   status (JFOF_OK if no kernel reported an error). */
+int jfof_sync(jfof_ctx *ctx);
+
+/* Static description of a status code. */
+const char *jfof_strerror(int code);
+
+/* Test hook for the bounded device loops: maximum iterations of every
+   union-find retry loop (default 1<<24; 0 restores the default).  A loop that
+   runs out latches JFOF_ETIMEOUT and returns. */
+int jfof_set_loop_budget(jfof_ctx *ctx, int64_t iterations);
+
+/* Per-launch tracing: with tracing on, every kernel the library launches is
+   bracketed by CUDA events recorded on the context's stream.  jfof_trace_read
+   synchronises the stream and writes one text line per kernel name,
+   "name launches total_ms", into buf (at most len bytes, NUL-terminated), then
+   forgets the records.  Returns JFOF_EOVERFLOW if buf is too small. */
+int jfof_trace_enable(jfof_ctx *ctx, int on);
+int jfof_trace_read(jfof_ctx *ctx, char *buf, size_t len, size_t *written);
+
+/* ---------------------------------------------------------------------- */
+/* Grid choice (Sec. 2.2, Algorithm 2 "Grid setup").                        */
+/* The linked-cell grid has n cells per axis with cell side L/n >= 1.01 b,  */
+/* so every pair within b lies in the same or adjacent cells (the printed   */
+/* n = ceil(L/b) gives cells smaller than b; see the design notes).  n is 1 */
+/* or >= 3.  Labels do not depend on n; it only changes speed.             */
+
+/* Largest legal n for (L, b), capped at 1600. */
+int jfof_max_cells_per_axis(float L, float b, int32_t *n_axis);
+
+/* Default n for N particles: the largest legal n with n^3 <= N (at least 1). */
+int jfof_default_cells_per_axis(int64_t N, float L, float b, int32_t *n_axis);
+
+/* ---------------------------------------------------------------------- */
+/* Plain FoF pipeline.                                                      */
+
+/* Cell structure produced by jfof_bin_cells.  Its pointers point into the
+   caller's workspace; the struct itself is plain data the caller keeps. */
+typedef struct {
+    int64_t n;            /* particles */
+    int32_t n_axis;       /* cells per axis */
+    int32_t brick;        /* cells per brick side (cell table is brick-major) */
+    float L, b;           /* box side and linking length */
+    uint32_t flags;       /* flags given to jfof_bin_cells */
+    void *spos;           /* device float4[n]: positions in cell order; .w holds the
+                             bits of the int32 original index */
+    uint32_t *cell_start; /* device [n_cells_table + 1]: start of each cell in spos */
+    int64_t n_cells_table;/* entries of the brick-major cell table */
+    void *scratch;        /* device scratch (>= 16 n bytes) reused by jfof_link */
+} jfof_cells;
+
+/* Bytes of workspace for jfof_bin_cells + jfof_link with N particles and
+   n_axis cells per axis. */
+int jfof_fof_bytes(int64_t N, int32_t n_axis, size_t *bytes);
+
+/* a1-a3: optional wrap, cell binning (cell key ix + n(iy + n iz) grouped into
+   bricks of 16^3 cells), and a two-level counting sort of the particles by
+   cell.  pos: device float32 [N,3].  Fills *cells (views into ws).
+   Sec. 2 step (i); Algorithm 2 "Wrap positions", "Cell indexing",
+   "Sort by cell".  Latches JFOF_ERANGE for a position outside [0, L)
+   without JFOF_WRAP. */
+int jfof_bin_cells(jfof_ctx *ctx, const float *pos, int64_t N, float L, float b,
+                   int32_t n_axis, uint32_t flags, void *ws, size_t ws_bytes,
+                   jfof_cells *cells);
+
+/* a4-a6: 27-cell neighbour scan (each unordered cell pair once), link test
+   d2 <= b*b with d2 = (dx*dx + dy*dy) + dz*dz in binary32 without FMA on
+   minimum-image differences, lock-free union-find, and the raw label
+   label[i] = smallest original index in i's component, in original order.
+   label: device int32 [N].  Sec. 2 steps (iii)-(v); Algorithm 2. */
+int jfof_link(jfof_ctx *ctx, const jfof_cells *cells, int32_t *label);
+
+/* Bytes of workspace for jfof_groups with N particles. */
+int jfof_groups_bytes(int64_t N, size_t *bytes);
+
+/* a7: compaction, histogram and minimum-size cut (Sec. 2 step (vi)).
+   label: device int32 [N] raw labels (smallest member index).
+   Outputs (device):
+     halo_id   [N]       halo of each particle, ascending by raw label, -1 if
+                         its group has fewer than min_size members;
+     count     [H_cap]   members per halo;
+     halo_start[H_cap+1] CSR offsets of members;
+     members   [N]       original indices grouped by halo, ascending within a
+                         halo (only the first halo_start[H] entries are used);
+     n_halos   [1]       H.
+   H_cap = N / min_size (the most halos that can exist). */
+int jfof_groups(jfof_ctx *ctx, const int32_t *label, int64_t N, int32_t min_size,
+                void *ws, size_t ws_bytes, int32_t *halo_id, int32_t *count,
+                int32_t *halo_start, int32_t *members, int32_t *n_halos);
+
+/* a8: halo properties (Sec. 3.1, Eq. 4; Table 1), binary32 with compensated
+   sums in a fixed order (deterministic):
+     mass[h]  = particle_mass * n_h
+     com[h]   = wrap(x_r + (1/n_h) sum_i mi(x_i - x_r)), r = smallest member
+     vmean[h] = (1/n_h) sum_i v_i
+     sigv[h]  = sqrt((1/(3 n_h)) sum_i |v_i - vmean_h|^2)
+   pos, vel: device float32 [N,3] (vel may be NULL: vmean and sigv untouched);
+   positions are wrapped as in jfof_bin_cells when flags has JFOF_WRAP.
+   halo_start, members, n_halos: from jfof_groups.  Outputs [H_cap] / [H_cap,3];
+   entries h >= H are left untouched. */
+int jfof_halo_props(jfof_ctx *ctx, const float *pos, const float *vel, int64_t N,
+                    float L, uint32_t flags, const int32_t *halo_start,
+                    const int32_t *members, const int32_t *n_halos, int64_t H_cap,
+                    float particle_mass, float *mass, float *com, float *vmean,
+                    float *sigv);
+
+/* a9: frozen-assignment adjoint (Sec. 3.1, Eq. 4): with memberships fixed,
+     g_pos_i = g_com[h] / n_h
+     g_vel_i = g_vmean[h] / n_h + g_sigv[h] (v_i - vmean_h) / (3 n_h sigv_h)
+   (the sigma term is 0 when sigv_h = 0); 0 for particles with halo_id -1.
+   Any of g_com [H,3], g_vmean [H,3], g_sigv [H] may be NULL (zero).  vel,
+   vmean and sigv may be NULL only when g_sigv is NULL.  Outputs g_pos,
+   g_vel: device float32 [N,3] (either may be NULL to skip it). */
+int jfof_halo_props_backward(jfof_ctx *ctx, const float *vel, const int32_t *halo_id,
+                             const int32_t *count, int64_t N, const float *vmean,
+                             const float *sigv, const float *g_com,
+                             const float *g_vmean, const float *g_sigv, float *g_pos,
+                             float *g_vel);
+
+/* Convenience: a1-a7 in one call (bin, link, groups) with one workspace. */
+int jfof_fof_all_bytes(int64_t N, int32_t n_axis, size_t *bytes);
+int jfof_fof(jfof_ctx *ctx, const float *pos, int64_t N, float L, float b, int32_t n_axis,
+             uint32_t flags, int32_t min_size, void *ws, size_t ws_bytes, int32_t *label,
+             int32_t *halo_id, int32_t *count, int32_t *halo_start, int32_t *members,
+             int32_t *n_halos);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JFOF_H */

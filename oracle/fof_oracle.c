@@ -164,9 +164,103 @@ static int32_t cell_coord(float x, float inv_cell, int32_t n)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Cell list: particles counting-sorted by cell id c = ix + n(iy + n iz), with */
+/* their positions copied in that order so that a cell is one contiguous run. */
+
+typedef struct {
+    int32_t n;
+    int64_t ncell;
+    int64_t *start;  /* [ncell + 1] */
+    int32_t *idx;    /* [N] original index, cell order, ascending within a cell */
+    float *cpos;     /* [3N] positions in cell order */
+} cell_list;
+
+static void cell_list_free(cell_list *cl)
+{
+    free(cl->start);
+    free(cl->idx);
+    free(cl->cpos);
+}
+
+static int cell_list_build(cell_list *cl, const float *pos, int64_t N, float L, int32_t n)
+{
+    cl->n = n;
+    cl->ncell = (int64_t)n * n * n;
+    cl->start = (int64_t *)calloc((size_t)cl->ncell + 1, sizeof(int64_t));
+    cl->idx = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    cl->cpos = (float *)malloc(sizeof(float) * 3 * (size_t)N);
+    int64_t *cid = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+    if (!cl->start || !cl->idx || !cl->cpos || !cid) {
+        free(cid);
+        cell_list_free(cl);
+        return ORC_ENOMEM;
+    }
+    float inv_cell = (float)((double)n / (double)L);
+    for (int64_t i = 0; i < N; ++i) {
+        int32_t ix = cell_coord(pos[3 * i + 0], inv_cell, n);
+        int32_t iy = cell_coord(pos[3 * i + 1], inv_cell, n);
+        int32_t iz = cell_coord(pos[3 * i + 2], inv_cell, n);
+        cid[i] = ix + (int64_t)n * (iy + (int64_t)n * iz);
+        cl->start[cid[i] + 1] += 1;
+    }
+    for (int64_t c = 0; c < cl->ncell; ++c)
+        cl->start[c + 1] += cl->start[c];
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)cl->ncell);
+    if (!fill) {
+        free(cid);
+        cell_list_free(cl);
+        return ORC_ENOMEM;
+    }
+    memcpy(fill, cl->start, sizeof(int64_t) * (size_t)cl->ncell);
+    for (int64_t i = 0; i < N; ++i) { /* ascending i: stable within a cell */
+        int64_t k = fill[cid[i]]++;
+        cl->idx[k] = (int32_t)i;
+        cl->cpos[3 * k + 0] = pos[3 * i + 0];
+        cl->cpos[3 * k + 1] = pos[3 * i + 1];
+        cl->cpos[3 * k + 2] = pos[3 * i + 2];
+    }
+    free(fill);
+    free(cid);
+    return ORC_OK;
+}
+
+/* The distinct cells among the 27 neighbours (. mod n) of cell (ix,iy,iz). */
+static int neighbour_cells(const cell_list *cl, int64_t c, int64_t out[27])
+{
+    int32_t n = cl->n;
+    int32_t ix = (int32_t)(c % n), iy = (int32_t)((c / n) % n), iz = (int32_t)(c / ((int64_t)n * n));
+    int cnt = 0;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                int32_t cx = ((ix + dx) % n + n) % n;
+                int32_t cy = ((iy + dy) % n + n) % n;
+                int32_t cz = ((iz + dz) % n + n) % n;
+                int64_t nc = cx + (int64_t)n * (cy + (int64_t)n * cz);
+                int dup = 0;
+                for (int s = 0; s < cnt; ++s)
+                    if (out[s] == nc)
+                        dup = 1;
+                if (!dup)
+                    out[cnt++] = nc;
+            }
+    return cnt;
+}
+
+/* Default grid for the oracle: the largest legal n with n^3 <= 16 N. */
+static int32_t oracle_grid(int64_t N, float L, float b)
+{
+    int32_t n = orc_max_cells_per_axis(L, b);
+    while (n > 3 && (double)n * n * n > 16.0 * (double)N)
+        --n;
+    return n;
+}
+
+/* ------------------------------------------------------------------------ */
 /* FoF labels via a linked-cell grid + union-find (Sec. 2.2, Algorithm 2).    */
-/* label[i] = smallest index in i's component.  n_axis = 0 picks the largest  */
-/* legal grid capped so that n^3 <= 8 N.  Returns ORC_* status.               */
+/* label[i] = smallest index in i's component.  n_axis = 0 picks a default    */
+/* grid.  Every pair (i, j), i < j, in the same or adjacent cells is tested   */
+/* once.  Returns ORC_* status.                                               */
 
 int orc_fof_labels(const float *pos, int64_t N, float L, float b, int32_t n_axis,
                    int32_t *label)
@@ -177,75 +271,37 @@ int orc_fof_labels(const float *pos, int64_t N, float L, float b, int32_t n_axis
         if (!(pos[i] >= 0.0f && pos[i] < L))
             return ORC_ERANGE;
     int32_t nmax = orc_max_cells_per_axis(L, b);
-    int32_t n = n_axis;
-    if (n <= 0) {
-        n = nmax;
-        while (n > 3 && (double)n * n * n > 8.0 * (double)N)
-            --n;
-    }
+    int32_t n = n_axis > 0 ? n_axis : oracle_grid(N, L, b);
     if (n > nmax || n == 2)
         return ORC_EINVAL;
-    int64_t ncell = (int64_t)n * n * n;
-    float inv_cell = (float)((double)n / (double)L);
-
-    int64_t *head = (int64_t *)malloc(sizeof(int64_t) * ncell);
-    int64_t *next = (int64_t *)malloc(sizeof(int64_t) * N);
+    cell_list cl;
+    int st = cell_list_build(&cl, pos, N, L, n);
+    if (st != ORC_OK)
+        return st;
     int32_t *parent = label; /* union-find forest lives in the output */
-    if (!head || !next) {
-        free(head);
-        free(next);
-        return ORC_ENOMEM;
-    }
-    for (int64_t c = 0; c < ncell; ++c)
-        head[c] = -1;
-    /* linked list per cell, built in descending index so that each list is
-       ascending in particle index */
-    for (int64_t i = N - 1; i >= 0; --i) {
-        int32_t ix = cell_coord(pos[3 * i + 0], inv_cell, n);
-        int32_t iy = cell_coord(pos[3 * i + 1], inv_cell, n);
-        int32_t iz = cell_coord(pos[3 * i + 2], inv_cell, n);
-        int64_t c = ix + (int64_t)n * (iy + (int64_t)n * iz);
-        next[i] = head[c];
-        head[c] = i;
-    }
     for (int64_t i = 0; i < N; ++i)
         parent[i] = (int32_t)i;
-
     float b2 = b * b;
-    for (int64_t i = 0; i < N; ++i) {
-        int32_t ix = cell_coord(pos[3 * i + 0], inv_cell, n);
-        int32_t iy = cell_coord(pos[3 * i + 1], inv_cell, n);
-        int32_t iz = cell_coord(pos[3 * i + 2], inv_cell, n);
-        /* the 27 neighbour cells with (. mod n) wrapping; duplicates removed
-           (only possible for n == 1) */
-        int64_t seen[27];
-        int nseen = 0;
-        for (int dz = -1; dz <= 1; ++dz)
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
-                    int32_t cx = ((ix + dx) % n + n) % n;
-                    int32_t cy = ((iy + dy) % n + n) % n;
-                    int32_t cz = ((iz + dz) % n + n) % n;
-                    int64_t c = cx + (int64_t)n * (cy + (int64_t)n * cz);
-                    int dup = 0;
-                    for (int s = 0; s < nseen; ++s)
-                        if (seen[s] == c)
-                            dup = 1;
-                    if (dup)
-                        continue;
-                    seen[nseen++] = c;
-                    for (int64_t j = head[c]; j >= 0; j = next[j]) {
-                        if (j <= i)
-                            continue; /* each unordered pair once */
-                        if (orc_dist2(pos + 3 * i, pos + 3 * j, L) <= b2)
-                            uf_union(parent, (int32_t)i, (int32_t)j);
-                    }
+    for (int64_t c = 0; c < cl.ncell; ++c) {
+        if (cl.start[c] == cl.start[c + 1])
+            continue;
+        int64_t nb[27];
+        int nnb = neighbour_cells(&cl, c, nb);
+        for (int64_t a = cl.start[c]; a < cl.start[c + 1]; ++a) {
+            int32_t i = cl.idx[a];
+            for (int s = 0; s < nnb; ++s)
+                for (int64_t k = cl.start[nb[s]]; k < cl.start[nb[s] + 1]; ++k) {
+                    int32_t j = cl.idx[k];
+                    if (j <= i)
+                        continue; /* each unordered pair once */
+                    if (orc_dist2(cl.cpos + 3 * a, cl.cpos + 3 * k, L) <= b2)
+                        uf_union(parent, i, j);
                 }
+        }
     }
     for (int64_t i = 0; i < N; ++i)
         label[i] = uf_find(parent, (int32_t)i);
-    free(head);
-    free(next);
+    cell_list_free(&cl);
     return ORC_OK;
 }
 
@@ -539,55 +595,38 @@ int64_t orc_pairs(const float *pos, int64_t N, float L, float b, float r_cut,
 {
     if (N < 1 || !(r_cut > 0.0f) || !(r_cut < 0.5f * L))
         return -1;
+    for (int64_t i = 0; i < 3 * N; ++i)
+        if (!(pos[i] >= 0.0f && pos[i] < L))
+            return -1;
     float rc2 = r_cut * r_cut;
     float b2 = b * b;
-    int32_t n = orc_max_cells_per_axis(L, r_cut);
-    while (n > 3 && (double)n * n * n > 8.0 * (double)N)
-        --n;
-    int64_t ncell = (int64_t)n * n * n;
-    float inv_cell = (float)((double)n / (double)L);
-    int64_t *head = (int64_t *)malloc(sizeof(int64_t) * ncell);
-    int64_t *next = (int64_t *)malloc(sizeof(int64_t) * N);
-    int32_t *buf = (int32_t *)malloc(sizeof(int32_t) * N);
-    if (!head || !next || !buf) {
-        free(head); free(next); free(buf);
+    cell_list cl;
+    if (cell_list_build(&cl, pos, N, L, oracle_grid(N, L, r_cut)) != ORC_OK)
+        return -1;
+    int64_t *where = (int64_t *)malloc(sizeof(int64_t) * (size_t)N); /* slot of index i */
+    int32_t *buf = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    if (!where || !buf) {
+        free(where); free(buf); cell_list_free(&cl);
         return -1;
     }
-    for (int64_t c = 0; c < ncell; ++c)
-        head[c] = -1;
-    for (int64_t i = N - 1; i >= 0; --i) {
-        int32_t ix = cell_coord(pos[3 * i + 0], inv_cell, n);
-        int32_t iy = cell_coord(pos[3 * i + 1], inv_cell, n);
-        int32_t iz = cell_coord(pos[3 * i + 2], inv_cell, n);
-        int64_t c = ix + (int64_t)n * (iy + (int64_t)n * iz);
-        next[i] = head[c];
-        head[c] = i;
-    }
+    for (int64_t a = 0; a < N; ++a)
+        where[cl.idx[a]] = a;
     int64_t E = 0;
     for (int64_t i = 0; i < N; ++i) {
-        int32_t ix = cell_coord(pos[3 * i + 0], inv_cell, n);
-        int32_t iy = cell_coord(pos[3 * i + 1], inv_cell, n);
-        int32_t iz = cell_coord(pos[3 * i + 2], inv_cell, n);
-        int64_t seen[27];
-        int nseen = 0, nb = 0;
-        for (int dz = -1; dz <= 1; ++dz)
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
-                    int32_t cx = ((ix + dx) % n + n) % n;
-                    int32_t cy = ((iy + dy) % n + n) % n;
-                    int32_t cz = ((iz + dz) % n + n) % n;
-                    int64_t c = cx + (int64_t)n * (cy + (int64_t)n * cz);
-                    int dup = 0;
-                    for (int s = 0; s < nseen; ++s)
-                        if (seen[s] == c)
-                            dup = 1;
-                    if (dup)
-                        continue;
-                    seen[nseen++] = c;
-                    for (int64_t j = head[c]; j >= 0; j = next[j])
-                        if (j > i && orc_dist2(pos + 3 * i, pos + 3 * j, L) < rc2)
-                            buf[nb++] = (int32_t)j;
-                }
+        int64_t a = where[i];
+        float *pa = cl.cpos + 3 * a;
+        int32_t n = cl.n;
+        float inv_cell = (float)((double)n / (double)L);
+        int64_t c = cell_coord(pa[0], inv_cell, n) +
+                    (int64_t)n * (cell_coord(pa[1], inv_cell, n) + (int64_t)n * cell_coord(pa[2], inv_cell, n));
+        int64_t nbc[27];
+        int nnb = neighbour_cells(&cl, c, nbc), nb = 0;
+        for (int s = 0; s < nnb; ++s)
+            for (int64_t k = cl.start[nbc[s]]; k < cl.start[nbc[s] + 1]; ++k) {
+                int32_t j = cl.idx[k];
+                if (j > i && orc_dist2(pa, cl.cpos + 3 * k, L) < rc2)
+                    buf[nb++] = j;
+            }
         qsort(buf, (size_t)nb, sizeof(int32_t), cmp_i32);
         for (int s = 0; s < nb; ++s) {
             if (E < cap) {
@@ -602,7 +641,7 @@ int64_t orc_pairs(const float *pos, int64_t N, float L, float b, float r_cut,
             ++E;
         }
     }
-    free(head); free(next); free(buf);
+    free(where); free(buf); cell_list_free(&cl);
     return E;
 }
 

@@ -1,0 +1,372 @@
+"""GB300-native Friends-of-Friends hot path (jFoF, arXiv 2510.26851).
+
+Thin Python binding over the C ABI in ``include/jfof.h`` (``_build/libjfof.so``,
+hand-written sm_103a kernels).  This module only marshals arguments: every step
+of the path runs in the library's CUDA kernels.  There is no CPU fallback: if
+the library is missing or no GPU is present, calls raise.
+
+PyTorch supplies device memory (tensors) and the current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libjfof.so")
+
+JFOF_OK, JFOF_EINVAL, JFOF_ERANGE, JFOF_ENOMEM, JFOF_ECUDA, JFOF_ETIMEOUT, JFOF_EOVERFLOW = range(7)
+JFOF_WRAP = 1
+
+# Every symbol the header declares (checked by the tests).
+EXPORTED = [
+    "jfof_create", "jfof_destroy", "jfof_set_stream", "jfof_sync", "jfof_strerror",
+    "jfof_set_loop_budget", "jfof_trace_enable", "jfof_trace_read", "jfof_max_cells_per_axis", "jfof_default_cells_per_axis",
+    "jfof_fof_bytes", "jfof_bin_cells", "jfof_link", "jfof_groups_bytes", "jfof_groups",
+    "jfof_halo_props", "jfof_halo_props_backward", "jfof_fof_all_bytes", "jfof_fof",
+]
+
+
+class JfofError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} (status {code})")
+
+
+class Cells(ctypes.Structure):
+    """Mirror of ``jfof_cells`` (views into the caller's workspace)."""
+    _fields_ = [("n", ctypes.c_int64), ("n_axis", ctypes.c_int32), ("brick", ctypes.c_int32),
+                ("L", ctypes.c_float), ("b", ctypes.c_float), ("flags", ctypes.c_uint32),
+                ("spos", ctypes.c_void_p), ("cell_start", ctypes.c_void_p),
+                ("n_cells_table", ctypes.c_int64), ("scratch", ctypes.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+_ctx = {}
+
+
+def _declare(lib):
+    c = ctypes
+    vp, i32, i64, u32, f32, sz = c.c_void_p, c.c_int32, c.c_int64, c.c_uint32, c.c_float, c.c_size_t
+    P = c.POINTER
+    sig = {
+        "jfof_create": [P(vp), c.c_int, vp],
+        "jfof_destroy": [vp],
+        "jfof_set_stream": [vp, vp],
+        "jfof_sync": [vp],
+        "jfof_set_loop_budget": [vp, i64],
+        "jfof_trace_enable": [vp, c.c_int],
+        "jfof_trace_read": [vp, c.c_char_p, sz, P(sz)],
+        "jfof_max_cells_per_axis": [f32, f32, P(i32)],
+        "jfof_default_cells_per_axis": [i64, f32, f32, P(i32)],
+        "jfof_fof_bytes": [i64, i32, P(sz)],
+        "jfof_bin_cells": [vp, vp, i64, f32, f32, i32, u32, vp, sz, P(Cells)],
+        "jfof_link": [vp, P(Cells), vp],
+        "jfof_groups_bytes": [i64, P(sz)],
+        "jfof_groups": [vp, vp, i64, i32, vp, sz, vp, vp, vp, vp, vp],
+        "jfof_halo_props": [vp, vp, vp, i64, f32, u32, vp, vp, vp, i64, f32, vp, vp, vp, vp],
+        "jfof_halo_props_backward": [vp, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp],
+        "jfof_fof_all_bytes": [i64, i32, P(sz)],
+        "jfof_fof": [vp, vp, i64, f32, f32, i32, u32, i32, vp, sz, vp, vp, vp, vp, vp, vp],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = c.c_int
+    lib.jfof_strerror.argtypes = [c.c_int]
+    lib.jfof_strerror.restype = c.c_char_p
+    return lib
+
+
+def library():
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libjfof.so not built ({LIB_PATH}); run "
+                                   "python -m paper_2510_26851_gb300.build")
+            _lib = _declare(ctypes.CDLL(LIB_PATH))
+        return _lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return library().jfof_strerror(code).decode()
+    except RuntimeError:
+        return f"status {code}"
+
+
+def _check(code: int, where: str):
+    if code != JFOF_OK:
+        raise JfofError(code, where)
+
+
+def context(device=None):
+    """Per-device library context bound to torch's current stream."""
+    if not torch.cuda.is_available():
+        raise RuntimeError("jfof needs a CUDA GPU; there is no CPU fallback")
+    dev = torch.cuda.current_device() if device is None else torch.device(device).index
+    dev = 0 if dev is None else dev
+    lib = library()
+    with _lock:
+        h = _ctx.get(dev)
+        if h is None:
+            h = ctypes.c_void_p()
+            _check(lib.jfof_create(ctypes.byref(h), dev, None), "jfof_create")
+            _ctx[dev] = h
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    _check(lib.jfof_set_stream(h, ctypes.c_void_p(stream)), "jfof_set_stream")
+    return h
+
+
+def sync(device=None):
+    """Wait for queued work; raise the latched device error, if any."""
+    h = context(device)
+    _check(library().jfof_sync(h), "device status")
+
+
+def set_loop_budget(iterations: int, device=None):
+    _check(library().jfof_set_loop_budget(context(device), int(iterations)), "jfof_set_loop_budget")
+
+
+def trace_enable(on: bool = True, device=None):
+    """Record CUDA events around every library kernel launch."""
+    _check(library().jfof_trace_enable(context(device), 1 if on else 0), "jfof_trace_enable")
+
+
+def trace_read(device=None) -> dict:
+    """Synchronise and return {kernel: (launches, total_ms)} since the last read."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    n = ctypes.c_size_t()
+    _check(library().jfof_trace_read(context(device), buf, len(buf), ctypes.byref(n)),
+           "jfof_trace_read")
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, cnt, ms = line.split()
+        out[name] = (int(cnt), float(ms))
+    return out
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _need(t, dtype, shape=None, name="tensor"):
+    if t is None:
+        return
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {shape}, got {tuple(t.shape)}")
+
+
+def max_cells_per_axis(L: float, b: float) -> int:
+    n = ctypes.c_int32()
+    _check(library().jfof_max_cells_per_axis(L, b, ctypes.byref(n)), "jfof_max_cells_per_axis")
+    return n.value
+
+
+def default_cells_per_axis(N: int, L: float, b: float) -> int:
+    n = ctypes.c_int32()
+    _check(library().jfof_default_cells_per_axis(N, L, b, ctypes.byref(n)),
+           "jfof_default_cells_per_axis")
+    return n.value
+
+
+def fof_bytes(N: int, n_axis: int) -> int:
+    s = ctypes.c_size_t()
+    _check(library().jfof_fof_bytes(N, n_axis, ctypes.byref(s)), "jfof_fof_bytes")
+    return s.value
+
+
+def groups_bytes(N: int) -> int:
+    s = ctypes.c_size_t()
+    _check(library().jfof_groups_bytes(N, ctypes.byref(s)), "jfof_groups_bytes")
+    return s.value
+
+
+def _ws(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+@dataclass
+class CellGrid:
+    cells: Cells
+    workspace: torch.Tensor  # keeps the memory the views point into alive
+
+
+def bin_cells(pos: torch.Tensor, L: float, b: float, n_axis: int = 0, wrap: bool = False,
+              workspace: torch.Tensor | None = None) -> CellGrid:
+    """a1-a3: wrap (optional), cell binning and counting sort by cell."""
+    _need(pos, torch.float32, None, "pos")
+    N = pos.shape[0]
+    n = default_cells_per_axis(N, L, b) if n_axis == 0 else int(n_axis)
+    need = fof_bytes(N, n)
+    ws = workspace if workspace is not None else _ws(need, pos.device)
+    cells = Cells()
+    h = context(pos.device)
+    _check(library().jfof_bin_cells(h, _ptr(pos), N, L, b, n, JFOF_WRAP if wrap else 0,
+                                    _ptr(ws), ws.numel(), ctypes.byref(cells)), "jfof_bin_cells")
+    return CellGrid(cells, ws)
+
+
+def link(grid: CellGrid, label: torch.Tensor | None = None) -> torch.Tensor:
+    """a4-a6: neighbour scan + union-find; raw labels (smallest member index)."""
+    N = grid.cells.n
+    dev = grid.workspace.device
+    if label is None:
+        label = torch.empty(N, dtype=torch.int32, device=dev)
+    _need(label, torch.int32, (N,), "label")
+    _check(library().jfof_link(context(dev), ctypes.byref(grid.cells), _ptr(label)), "jfof_link")
+    return label
+
+
+@dataclass
+class Groups:
+    halo_id: torch.Tensor     # [N] int32, -1 below the cut
+    count: torch.Tensor       # [H_cap] int32 (first H valid)
+    halo_start: torch.Tensor  # [H_cap+1] int32
+    members: torch.Tensor     # [N] int32 (first halo_start[H] valid)
+    n_halos_dev: torch.Tensor # [1] int32 on the device
+    H_cap: int
+
+    @property
+    def n_halos(self) -> int:
+        return int(self.n_halos_dev.item())
+
+
+def _alloc_groups(N: int, min_size: int, dev) -> Groups:
+    H_cap = max(N // min_size, 1)
+    return Groups(torch.empty(N, dtype=torch.int32, device=dev),
+                  torch.empty(H_cap, dtype=torch.int32, device=dev),
+                  torch.empty(H_cap + 1, dtype=torch.int32, device=dev),
+                  torch.empty(N, dtype=torch.int32, device=dev),
+                  torch.empty(1, dtype=torch.int32, device=dev), H_cap)
+
+
+def groups(label: torch.Tensor, min_size: int = 20, workspace: torch.Tensor | None = None) -> Groups:
+    """a7: compaction, histogram, minimum-size cut, CSR members."""
+    _need(label, torch.int32, None, "label")
+    N = label.shape[0]
+    dev = label.device
+    g = _alloc_groups(N, min_size, dev)
+    ws = workspace if workspace is not None else _ws(groups_bytes(N), dev)
+    _check(library().jfof_groups(context(dev), _ptr(label), N, min_size, _ptr(ws), ws.numel(),
+                                 _ptr(g.halo_id), _ptr(g.count), _ptr(g.halo_start),
+                                 _ptr(g.members), _ptr(g.n_halos_dev)), "jfof_groups")
+    return g
+
+
+@dataclass
+class FofResult:
+    label: torch.Tensor
+    groups: Groups
+    n_axis: int
+
+
+def fof_all_bytes(N: int, n_axis: int) -> int:
+    s = ctypes.c_size_t()
+    _check(library().jfof_fof_all_bytes(N, n_axis, ctypes.byref(s)), "jfof_fof_all_bytes")
+    return s.value
+
+
+def fof(pos: torch.Tensor, L: float, b: float, min_size: int = 20, n_axis: int = 0,
+        wrap: bool = False, workspace: torch.Tensor | None = None,
+        out: FofResult | None = None) -> FofResult:
+    """a1-a7 in one call: labels, halo ids, counts and CSR members.  ``out``
+    (from a previous call with the same N and min_size) is reused in place."""
+    _need(pos, torch.float32, None, "pos")
+    N = pos.shape[0]
+    dev = pos.device
+    n = default_cells_per_axis(N, L, b) if n_axis == 0 else int(n_axis)
+    ws = workspace if workspace is not None else _ws(fof_all_bytes(N, n), dev)
+    if out is not None:
+        label, g = out.label, out.groups
+    else:
+        label = torch.empty(N, dtype=torch.int32, device=dev)
+        g = _alloc_groups(N, min_size, dev)
+    _check(library().jfof_fof(context(dev), _ptr(pos), N, L, b, n, JFOF_WRAP if wrap else 0,
+                              min_size, _ptr(ws), ws.numel(), _ptr(label), _ptr(g.halo_id),
+                              _ptr(g.count), _ptr(g.halo_start), _ptr(g.members),
+                              _ptr(g.n_halos_dev)), "jfof_fof")
+    return FofResult(label, g, n)
+
+
+@dataclass
+class Props:
+    mass: torch.Tensor   # [H_cap]
+    com: torch.Tensor    # [H_cap, 3]
+    vmean: torch.Tensor  # [H_cap, 3]
+    sigv: torch.Tensor   # [H_cap]
+
+
+def halo_props(pos: torch.Tensor, vel: torch.Tensor | None, L: float, g: Groups,
+               particle_mass: float = 1.0, wrap: bool = False, out: Props | None = None) -> Props:
+    """a8: mass, periodic COM, velocity mean and dispersion (first H rows valid)."""
+    _need(pos, torch.float32, None, "pos")
+    _need(vel, torch.float32, tuple(pos.shape), "vel")
+    dev = pos.device
+    H = g.H_cap
+    if out is None:
+        out = Props(torch.zeros(H, device=dev), torch.zeros(H, 3, device=dev),
+                    torch.zeros(H, 3, device=dev), torch.zeros(H, device=dev))
+    _check(library().jfof_halo_props(context(dev), _ptr(pos), _ptr(vel), pos.shape[0], L,
+                                     JFOF_WRAP if wrap else 0, _ptr(g.halo_start), _ptr(g.members),
+                                     _ptr(g.n_halos_dev), g.H_cap, particle_mass, _ptr(out.mass),
+                                     _ptr(out.com), _ptr(out.vmean), _ptr(out.sigv)),
+           "jfof_halo_props")
+    return out
+
+
+def halo_props_backward(vel, g: Groups, vmean, sigv, g_com=None, g_vmean=None, g_sigv=None):
+    """a9: frozen-assignment adjoint -> (g_pos[N,3], g_vel[N,3])."""
+    dev = g.halo_id.device
+    N = g.halo_id.shape[0]
+    g_pos = torch.empty(N, 3, device=dev)
+    g_vel = torch.empty(N, 3, device=dev)
+    _check(library().jfof_halo_props_backward(
+        context(dev), _ptr(vel), _ptr(g.halo_id), _ptr(g.count), N, _ptr(vmean), _ptr(sigv),
+        _ptr(g_com), _ptr(g_vmean), _ptr(g_sigv), _ptr(g_pos), _ptr(g_vel)),
+        "jfof_halo_props_backward")
+    return g_pos, g_vel
+
+
+class HaloProps(torch.autograd.Function):
+    """Differentiable halo properties with frozen memberships (Sec. 3.1).
+
+    forward(pos, vel, groups, L) -> (com[H,3], vmean[H,3], sigv[H]) for the H
+    halos of ``groups``; backward runs the adjoint kernel.  Memberships (the
+    FoF labels) are not differentiated.
+    """
+
+    @staticmethod
+    def forward(ctx, pos, vel, g: Groups, L: float, wrap: bool = False):
+        H = g.n_halos
+        p = halo_props(pos.detach().contiguous(), vel.detach().contiguous(), L, g, wrap=wrap)
+        ctx.g = g
+        vm, sg = p.vmean[:H].contiguous(), p.sigv[:H].contiguous()
+        ctx.save_for_backward(vel.detach(), p.vmean, p.sigv)
+        ctx.H = H
+        return p.com[:H].clone(), vm, sg
+
+    @staticmethod
+    def backward(ctx, g_com, g_vmean, g_sigv):
+        vel, vmean, sigv = ctx.saved_tensors
+        g = ctx.g
+        H, Hc = ctx.H, g.H_cap
+
+        def pad(t, shape):
+            if t is None:
+                return None
+            out = torch.zeros(shape, device=vel.device, dtype=torch.float32)
+            out[:H] = t
+            return out.contiguous()
+        gp, gv = halo_props_backward(vel, g, vmean, sigv, pad(g_com, (Hc, 3)),
+                                     pad(g_vmean, (Hc, 3)), pad(g_sigv, (Hc,)))
+        return gp, gv, None, None, None

@@ -1,0 +1,294 @@
+// api.cu -- the C ABI (include/jfof.h): argument checks, workspace layout,
+// launches on the context's stream, and the latched device status.
+#include <cmath>
+#include <cstring>
+
+#include "jfof_internal.cuh"
+#include "k_fof.cuh"
+
+using namespace jfof;
+
+namespace {
+
+constexpr int32_t kMaxCellsPerAxis = 1600;
+
+bool finite_pos(float x) { return std::isfinite(x) && x > 0.0f; }
+
+int check_box(int64_t N, float L, float b) {
+    if (N < 1 || N > int64_t(INT32_MAX)) return JFOF_EINVAL;
+    if (!finite_pos(L) || !finite_pos(b)) return JFOF_EINVAL;
+    if (!(double(b) < 0.5 * double(L))) return JFOF_EINVAL;
+    return JFOF_OK;
+}
+
+int32_t max_cells(float L, float b) {
+    double m = std::floor(double(L) / (1.01 * double(b)));
+    if (m < 1.0) m = 1.0;
+    if (m > kMaxCellsPerAxis) m = kMaxCellsPerAxis;
+    int32_t n = int32_t(m);
+    if (n == 2) n = 1;
+    return n;
+}
+
+int resolve_n(int64_t N, float L, float b, int32_t n_axis, int32_t *out) {
+    int32_t nmax = max_cells(L, b);
+    if (n_axis == 0) {
+        int32_t n = nmax;
+        while (n > 3 && double(n) * n * n > double(N)) --n;
+        *out = n;
+        return JFOF_OK;
+    }
+    if (n_axis < 0 || n_axis == 2 || n_axis > nmax) return JFOF_EINVAL;
+    *out = n_axis;
+    return JFOF_OK;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? JFOF_OK : JFOF_ECUDA; }
+
+int launch_status() { return cuda_status(cudaGetLastError()); }
+
+}  // namespace
+
+namespace jfof {
+
+size_t fof_layout(int64_t N, int n, FofBuffers *fb, void *base) {
+    char *p = reinterpret_cast<char *>(base);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char *q = p ? p + off : nullptr;
+        off += align_up(bytes);
+        return q;
+    };
+    int64_t nb = bricks_per_axis(n);
+    int64_t n_bricks = nb * nb * nb;
+    FofBuffers f;
+    f.spos = reinterpret_cast<float4 *>(take(sizeof(float4) * size_t(N)));
+    f.cell_start = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * size_t(cell_table_entries(n) + 1)));
+    f.brick_count = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * size_t(n_bricks + 1)));
+    f.brick_start = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * size_t(n_bricks + 1)));
+    f.cursor = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * size_t(n_bricks + 1)));
+    f.scan_tmp = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * scan_tmp_words(n_bricks)));
+    // bin scatter buffer; reused by the link as parent[N] + rootmin[N]
+    size_t scratch = sizeof(float4) * size_t(N);
+    size_t link_need = sizeof(int) * (align_up(size_t(N), 64) + size_t(N));
+    f.tmp = reinterpret_cast<float4 *>(take(scratch > link_need ? scratch : link_need));
+    if (fb) *fb = f;
+    return off;
+}
+
+}  // namespace jfof
+
+extern "C" {
+
+const char *jfof_strerror(int code) {
+    switch (code) {
+        case JFOF_OK: return "ok";
+        case JFOF_EINVAL: return "invalid argument";
+        case JFOF_ERANGE: return "position outside [0, L) (or not finite) without JFOF_WRAP";
+        case JFOF_ENOMEM: return "workspace too small";
+        case JFOF_ECUDA: return "CUDA runtime error";
+        case JFOF_ETIMEOUT: return "bounded device loop ran out of iterations";
+        case JFOF_EOVERFLOW: return "output capacity too small";
+        default: return "unknown status";
+    }
+}
+
+int jfof_create(jfof_ctx **ctx, int device, void *stream) {
+    if (!ctx) return JFOF_EINVAL;
+    *ctx = nullptr;
+    if (cudaSetDevice(device) != cudaSuccess) return JFOF_ECUDA;
+    jfof_ctx *c = new jfof_ctx();
+    c->device = device;
+    c->tracer = nullptr;
+    c->stream = reinterpret_cast<cudaStream_t>(stream);
+    c->loop_budget = kDefaultLoopBudget;
+    if (cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess) {
+        delete c;
+        return JFOF_ECUDA;
+    }
+    if (cudaMallocHost(&c->h_status, sizeof(int)) != cudaSuccess) {
+        cudaFree(c->d_status);
+        delete c;
+        return JFOF_ECUDA;
+    }
+    *c->h_status = 0;
+    if (cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess) {
+        cudaFree(c->d_status);
+        cudaFreeHost(c->h_status);
+        delete c;
+        return JFOF_ECUDA;
+    }
+    *ctx = c;
+    return JFOF_OK;
+}
+
+int jfof_destroy(jfof_ctx *ctx) {
+    if (!ctx) return JFOF_EINVAL;
+    jfof_trace_enable(ctx, 0);
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->d_status);
+    cudaFreeHost(ctx->h_status);
+    delete ctx;
+    return JFOF_OK;
+}
+
+int jfof_set_stream(jfof_ctx *ctx, void *stream) {
+    if (!ctx) return JFOF_EINVAL;
+    ctx->stream = reinterpret_cast<cudaStream_t>(stream);
+    return JFOF_OK;
+}
+
+int jfof_set_loop_budget(jfof_ctx *ctx, int64_t iterations) {
+    if (!ctx || iterations < 0) return JFOF_EINVAL;
+    ctx->loop_budget = iterations == 0 ? kDefaultLoopBudget : iterations;
+    return JFOF_OK;
+}
+
+int jfof_sync(jfof_ctx *ctx) {
+    if (!ctx) return JFOF_EINVAL;
+    cudaSetDevice(ctx->device);
+    if (cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+        return JFOF_ECUDA;
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return JFOF_ECUDA;
+    int st = *ctx->h_status;
+    if (st != 0) cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream);
+    return st;
+}
+
+int jfof_max_cells_per_axis(float L, float b, int32_t *n_axis) {
+    if (!n_axis || !finite_pos(L) || !finite_pos(b)) return JFOF_EINVAL;
+    *n_axis = max_cells(L, b);
+    return JFOF_OK;
+}
+
+int jfof_default_cells_per_axis(int64_t N, float L, float b, int32_t *n_axis) {
+    if (!n_axis) return JFOF_EINVAL;
+    int e = check_box(N, L, b);
+    if (e) return e;
+    return resolve_n(N, L, b, 0, n_axis);
+}
+
+int jfof_fof_bytes(int64_t N, int32_t n_axis, size_t *bytes) {
+    if (!bytes || N < 1 || N > int64_t(INT32_MAX) || n_axis < 1 || n_axis == 2 || n_axis > kMaxCellsPerAxis)
+        return JFOF_EINVAL;
+    *bytes = fof_layout(N, n_axis, nullptr, nullptr);
+    return JFOF_OK;
+}
+
+int jfof_bin_cells(jfof_ctx *ctx, const float *pos, int64_t N, float L, float b, int32_t n_axis, uint32_t flags,
+                   void *ws, size_t ws_bytes, jfof_cells *cells) {
+    if (!ctx || !pos || !ws || !cells) return JFOF_EINVAL;
+    int e = check_box(N, L, b);
+    if (e) return e;
+    int32_t n;
+    if ((e = resolve_n(N, L, b, n_axis, &n))) return e;
+    FofBuffers fb;
+    size_t need = fof_layout(N, n, &fb, ws);
+    if (ws_bytes < need) return JFOF_ENOMEM;
+    cudaSetDevice(ctx->device);
+    CtxScope scope(ctx);
+    launch_bin_cells(pos, N, L, n, (flags & JFOF_WRAP) != 0, fb, ctx->dev(), ctx->stream);
+    jfof_cells c;
+    c.n = N;
+    c.n_axis = n;
+    c.brick = kBrick;
+    c.L = L;
+    c.b = b;
+    c.flags = flags;
+    c.spos = fb.spos;
+    c.cell_start = fb.cell_start;
+    c.n_cells_table = cell_table_entries(n);
+    c.scratch = fb.tmp;
+    *cells = c;
+    return launch_status();
+}
+
+int jfof_link(jfof_ctx *ctx, const jfof_cells *cells, int32_t *label) {
+    if (!ctx || !cells || !label || !cells->spos || !cells->cell_start || !cells->scratch) return JFOF_EINVAL;
+    int e = check_box(cells->n, cells->L, cells->b);
+    if (e) return e;
+    if (cells->n_axis < 1 || cells->n_axis == 2 || cells->n_axis > max_cells(cells->L, cells->b)) return JFOF_EINVAL;
+    cudaSetDevice(ctx->device);
+    CtxScope scope(ctx);
+    launch_link(*cells, label, ctx->dev(), ctx->stream);
+    return launch_status();
+}
+
+int jfof_groups_bytes(int64_t N, size_t *bytes) {
+    if (!bytes || N < 1 || N > int64_t(INT32_MAX)) return JFOF_EINVAL;
+    *bytes = groups_layout(N, N, nullptr, nullptr);
+    return JFOF_OK;
+}
+
+int jfof_groups(jfof_ctx *ctx, const int32_t *label, int64_t N, int32_t min_size, void *ws, size_t ws_bytes,
+                int32_t *halo_id, int32_t *count, int32_t *halo_start, int32_t *members, int32_t *n_halos) {
+    if (!ctx || !label || !ws || !halo_id || !count || !halo_start || !members || !n_halos) return JFOF_EINVAL;
+    if (N < 1 || N > int64_t(INT32_MAX) || min_size < 1) return JFOF_EINVAL;
+    int64_t H_cap = N / min_size;
+    if (H_cap < 1) H_cap = 1;
+    GroupBuffers gb;
+    size_t need = groups_layout(N, H_cap, &gb, ws);
+    if (ws_bytes < need) return JFOF_ENOMEM;
+    cudaSetDevice(ctx->device);
+    CtxScope scope(ctx);
+    launch_groups(label, N, min_size, H_cap, gb, halo_id, count, halo_start, members, n_halos, ctx->dev(),
+                  ctx->stream);
+    return launch_status();
+}
+
+int jfof_halo_props(jfof_ctx *ctx, const float *pos, const float *vel, int64_t N, float L, uint32_t flags,
+                    const int32_t *halo_start, const int32_t *members, const int32_t *n_halos, int64_t H_cap,
+                    float particle_mass, float *mass, float *com, float *vmean, float *sigv) {
+    if (!ctx || !pos || !halo_start || !members || !n_halos || !mass || !com) return JFOF_EINVAL;
+    if (vel && (!vmean || !sigv)) return JFOF_EINVAL;
+    if (N < 1 || N > int64_t(INT32_MAX) || H_cap < 1 || !finite_pos(L)) return JFOF_EINVAL;
+    cudaSetDevice(ctx->device);
+    CtxScope scope(ctx);
+    launch_halo_props(pos, vel, N, L, (flags & JFOF_WRAP) != 0, halo_start, members, n_halos, H_cap, particle_mass,
+                      mass, com, vmean, sigv, ctx->stream);
+    return launch_status();
+}
+
+int jfof_halo_props_backward(jfof_ctx *ctx, const float *vel, const int32_t *halo_id, const int32_t *count,
+                             int64_t N, const float *vmean, const float *sigv, const float *g_com,
+                             const float *g_vmean, const float *g_sigv, float *g_pos, float *g_vel) {
+    if (!ctx || !halo_id || !count) return JFOF_EINVAL;
+    if (g_sigv && (!vel || !vmean || !sigv)) return JFOF_EINVAL;
+    if (N < 1 || N > int64_t(INT32_MAX)) return JFOF_EINVAL;
+    cudaSetDevice(ctx->device);
+    CtxScope scope(ctx);
+    launch_halo_props_backward(vel, halo_id, count, N, vmean, sigv, g_com, g_vmean, g_sigv, g_pos, g_vel,
+                               ctx->stream);
+    return launch_status();
+}
+
+int jfof_fof_all_bytes(int64_t N, int32_t n_axis, size_t *bytes) {
+    size_t a, g;
+    int e = jfof_fof_bytes(N, n_axis, &a);
+    if (e) return e;
+    if ((e = jfof_groups_bytes(N, &g))) return e;
+    *bytes = a + g;
+    return JFOF_OK;
+}
+
+int jfof_fof(jfof_ctx *ctx, const float *pos, int64_t N, float L, float b, int32_t n_axis, uint32_t flags,
+             int32_t min_size, void *ws, size_t ws_bytes, int32_t *label, int32_t *halo_id, int32_t *count,
+             int32_t *halo_start, int32_t *members, int32_t *n_halos) {
+    if (!ctx || !ws) return JFOF_EINVAL;
+    int e = check_box(N, L, b);
+    if (e) return e;
+    int32_t n;
+    if ((e = resolve_n(N, L, b, n_axis, &n))) return e;
+    size_t a = fof_layout(N, n, nullptr, nullptr);
+    size_t g;
+    jfof_groups_bytes(N, &g);
+    if (ws_bytes < a + g) return JFOF_ENOMEM;
+    jfof_cells cells;
+    if ((e = jfof_bin_cells(ctx, pos, N, L, b, n, flags, ws, a, &cells))) return e;
+    if ((e = jfof_link(ctx, &cells, label))) return e;
+    return jfof_groups(ctx, label, N, min_size, reinterpret_cast<char *>(ws) + a, g, halo_id, count, halo_start,
+                       members, n_halos);
+}
+
+}  // extern "C"

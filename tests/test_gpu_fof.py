@@ -1,0 +1,239 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle on the
+same seeded inputs.  Labels, halo ids, counts and CSR members must be
+bit-exact; properties and adjoints within the stated tolerances."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+# Tolerances (FP32 compensated sums against the FP64 oracle):
+COM_TOL = 1e-5      # periodic COM error as a fraction of L
+SIGV_RTOL = 1e-4    # velocity dispersion, relative
+VMEAN_TOL = 1e-5    # |vmean error| / mean |v| of the halo
+BWD_RTOL = 1e-4     # adjoint vs analytic FP64 adjoint, relative (with an absolute floor)
+
+
+@pytest.fixture(scope="module")
+def J():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_26851_gb300 import build
+    build.build()
+    import paper_2510_26851_gb300 as j
+    return j
+
+
+def run_fof(J, pos_np, L, b, min_size=20, n_axis=0, wrap=False):
+    pos = torch.from_numpy(np.ascontiguousarray(pos_np, np.float32)).cuda()
+    r = J.fof(pos, L, b, min_size=min_size, n_axis=n_axis, wrap=wrap)
+    J.sync()
+    H = r.groups.n_halos
+    return pos, r, H
+
+
+def check_groups(r, H, lab_ref, min_size):
+    hid_ref, cnt_ref = oracle.groups(lab_ref, min_size)
+    assert H == len(cnt_ref)
+    assert np.array_equal(r.groups.halo_id.cpu().numpy(), hid_ref)
+    assert np.array_equal(r.groups.count[:H].cpu().numpy(), cnt_ref)
+    hs = r.groups.halo_start[:H + 1].cpu().numpy()
+    assert hs[0] == 0 and np.array_equal(np.diff(hs), cnt_ref)
+    mem = r.groups.members[:hs[-1]].cpu().numpy()
+    order = np.argsort(hid_ref[hid_ref >= 0], kind="stable")
+    expect = np.nonzero(hid_ref >= 0)[0][order]
+    assert np.array_equal(mem, expect)
+    return hid_ref, cnt_ref
+
+
+def test_hand_cases(J):
+    for c in json.load(open(os.path.join(GOLDEN, "fof_hand_cases.json")))["cases"]:
+        pos = np.array(c["pos"], np.float32)
+        _, r, _ = run_fof(J, pos, c["L"], c["b"], min_size=1)
+        assert r.label.cpu().tolist() == c["labels"], c["name"]
+
+
+def test_small_clustered_box_bit_exact(J):
+    spec = synth.SMALL_32
+    pos, _ = synth.generate(spec, device="cuda")
+    pos_np = pos.cpu().numpy()
+    lab_ref = oracle.fof_labels(pos_np, spec.L, spec.b)
+    _, r, H = run_fof(J, pos_np, spec.L, spec.b, spec.min_size)
+    assert np.array_equal(r.label.cpu().numpy(), lab_ref)
+    check_groups(r, H, lab_ref, spec.min_size)
+    assert H > 50
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_labels_invariant_across_grids(J, seed):
+    N, L = 20000, 20.0
+    pos_np = synth.uniform(N, L, seed).numpy()
+    b = 0.8 * L / N ** (1 / 3)
+    lab_ref = oracle.fof_labels(pos_np, L, b)
+    nmax = J.max_cells_per_axis(L, b)
+    for n in sorted({1, 3, 4, 7, 16, 17, 33, nmax}):
+        if n > nmax:
+            continue
+        _, r, _ = run_fof(J, pos_np, L, b, 1, n_axis=n)
+        assert np.array_equal(r.label.cpu().numpy(), lab_ref), n
+
+
+def test_ragged_sizes_and_tiny_boxes(J):
+    rng = np.random.default_rng(0)
+    for N in (1, 2, 3, 31, 33, 255, 257, 4097):
+        L = 5.0
+        pos_np = rng.uniform(0, L, (N, 3)).astype(np.float32)
+        pos_np[pos_np >= L] = 0
+        b = 0.9 * L / max(N, 8) ** (1 / 3)
+        lab_ref = oracle.fof_brute(pos_np, L, b)
+        _, r, H = run_fof(J, pos_np, L, b, 2)
+        assert np.array_equal(r.label.cpu().numpy(), lab_ref), N
+        check_groups(r, H, lab_ref, 2)
+
+
+def test_lattice_closed_forms(J):
+    m = 16
+    idx = np.arange(m, dtype=np.float32)
+    gz, gy, gx = np.meshgrid(idx, idx, idx, indexing="ij")
+    pos_np = np.stack([gx, gy, gz], -1).reshape(-1, 3).astype(np.float32)
+    L = float(m)
+    _, r, H = run_fof(J, pos_np, L, 1.0 / 0.9, 20)
+    assert (r.label.cpu().numpy() == 0).all() and H == 1
+    assert r.groups.count[0].item() == m ** 3
+    assert np.array_equal(r.groups.members[:m ** 3].cpu().numpy(), np.arange(m ** 3))
+    _, r, H = run_fof(J, pos_np, L, 1.0 / 1.1, 1)
+    assert np.array_equal(r.label.cpu().numpy(), np.arange(m ** 3)) and H == m ** 3
+
+
+def test_wrap_flag_and_boundary(J):
+    rng = np.random.default_rng(4)
+    N, L, b = 30000, 12.0, 0.25
+    p = rng.uniform(-L, 2 * L, (N, 3)).astype(np.float32)
+    wrapped = oracle.wrap(p, L)
+    lab_ref = oracle.fof_labels(wrapped, L, b)
+    _, r, _ = run_fof(J, p, L, b, 1, wrap=True)
+    assert np.array_equal(r.label.cpu().numpy(), lab_ref)
+
+
+def test_out_of_range_latches_erange(J):
+    p = np.array([[1.0, 2.0, 3.0], [1.1, 2.0, 12.5]], np.float32)
+    pos = torch.from_numpy(p).cuda()
+    J.fof(pos, 10.0, 0.5, min_size=1)
+    with pytest.raises(J.JfofError) as e:
+        J.sync()
+    assert e.value.code == J.JFOF_ERANGE
+    J.sync()  # cleared
+
+
+def test_bad_arguments_rejected_on_host(J):
+    pos = torch.zeros(4, 3, device="cuda")
+    with pytest.raises(J.JfofError):
+        J.fof(pos, 10.0, 6.0)  # b >= L/2
+    with pytest.raises(J.JfofError):
+        J.fof(pos, 10.0, 0.5, n_axis=2)
+
+
+def test_union_find_budget_timeout_is_reported(J):
+    # a budget of one CAS retry per union cannot finish a dense cluster: the
+    # bounded loop gives up, latches JFOF_ETIMEOUT and returns
+    rng = np.random.default_rng(1)
+    p = (5.0 + rng.normal(0, 0.05, (20000, 3))).astype(np.float32)
+    pos = torch.from_numpy(p).cuda()
+    J.set_loop_budget(1)
+    try:
+        J.fof(pos, 10.0, 0.3, min_size=1)
+        with pytest.raises(J.JfofError) as e:
+            J.sync()
+        assert e.value.code == J.JFOF_ETIMEOUT
+    finally:
+        J.set_loop_budget(0)
+    J.fof(pos, 10.0, 0.3, min_size=1)
+    J.sync()
+
+
+def props_check(J, pos, vel, r, H, L, lab_ref, min_size):
+    hid_ref, cnt_ref = oracle.groups(lab_ref, min_size)
+    p = J.halo_props(pos, vel, L, r.groups, particle_mass=1.0)
+    J.sync()
+    pos64 = pos.cpu().numpy().astype(np.float64)
+    vel64 = vel.cpu().numpy().astype(np.float64)
+    m_ref, com_ref, vm_ref, sg_ref = oracle.halo_props(pos64, vel64, hid_ref, H, L)
+    assert np.array_equal(p.mass[:H].cpu().numpy(), m_ref.astype(np.float32))
+    com = p.com[:H].cpu().numpy().astype(np.float64)
+    dcom = np.abs((com - com_ref + L / 2) % L - L / 2) / L
+    assert dcom.max() <= COM_TOL, dcom.max()
+    assert ((com >= 0) & (com < L)).all()
+    sg = p.sigv[:H].cpu().numpy()
+    assert (np.abs(sg - sg_ref) <= SIGV_RTOL * np.abs(sg_ref) + 1e-30).all()
+    vm = p.vmean[:H].cpu().numpy()
+    absv = np.zeros(H)
+    np.add.at(absv, hid_ref[hid_ref >= 0], np.abs(vel64[hid_ref >= 0]).mean(1))
+    scale = absv / cnt_ref
+    assert (np.abs(vm - vm_ref).max(1) <= VMEAN_TOL * scale + 1e-6).all()
+    return p, hid_ref, cnt_ref, (m_ref, com_ref, vm_ref, sg_ref)
+
+
+def test_props_and_backward_clustered_box(J):
+    spec = synth.BoxSpec("t", 200_000, 60.0, synth.linking_length(60.0, 200_000), 1200, 0.6, 5)
+    pos, vel = synth.generate(spec, device="cuda")
+    pos_np = pos.cpu().numpy()
+    lab_ref = oracle.fof_labels(pos_np, spec.L, spec.b)
+    _, r, H = run_fof(J, pos_np, spec.L, spec.b, spec.min_size)
+    assert np.array_equal(r.label.cpu().numpy(), lab_ref)
+    p, hid_ref, cnt_ref, ref = props_check(J, pos, vel, r, H, spec.L, lab_ref, spec.min_size)
+    # adjoint with the C5a loss: g_com = 2 w com, g_sigv = 2 w sigma
+    w = torch.rand(H, generator=torch.Generator().manual_seed(1), dtype=torch.float64).numpy()
+    g_com = torch.zeros(r.groups.H_cap, 3, device="cuda")
+    g_sig = torch.zeros(r.groups.H_cap, device="cuda")
+    g_com[:H] = torch.from_numpy(2 * w[:, None] * p.com[:H].cpu().numpy()).float().cuda()
+    g_sig[:H] = torch.from_numpy(2 * w * p.sigv[:H].cpu().numpy()).float().cuda()
+    gp, gv = J.halo_props_backward(vel, r.groups, p.vmean, p.sigv, g_com=g_com, g_sigv=g_sig)
+    J.sync()
+    gp_ref, gv_ref = oracle.halo_props_backward(
+        vel.cpu().numpy().astype(np.float64), hid_ref, H, p.vmean[:H].cpu().numpy(),
+        p.sigv[:H].cpu().numpy(), g_com=g_com[:H].cpu().numpy(), g_sigv=g_sig[:H].cpu().numpy())
+    for got, want in ((gp.cpu().numpy(), gp_ref), (gv.cpu().numpy(), gv_ref)):
+        err = np.abs(got - want)
+        assert (err <= BWD_RTOL * np.abs(want) + 1e-6 * np.abs(want).max()).all(), err.max()
+
+
+def test_autograd_function(J):
+    spec = synth.BoxSpec("t", 50_000, 40.0, synth.linking_length(40.0, 50_000), 300, 0.6, 6)
+    pos, vel = synth.generate(spec, device="cuda")
+    r = J.fof(pos, spec.L, spec.b, spec.min_size)
+    pos = pos.clone().requires_grad_(True)
+    vel = vel.clone().requires_grad_(True)
+    com, vm, sg = J.HaloProps.apply(pos, vel, r.groups, spec.L)
+    H = com.shape[0]
+    w = torch.rand(H, device="cuda", generator=torch.Generator(device="cuda").manual_seed(0))
+    loss = (w * ((com ** 2).sum(1) + sg ** 2)).sum()
+    loss.backward()
+    J.sync()
+    hid = r.groups.halo_id.long()
+    cnt = r.groups.count[:H].float()
+    mem = hid >= 0
+    exp_gp = torch.zeros_like(pos)
+    exp_gp[mem] = (2 * w[:, None] * com.detach() / cnt[:, None])[hid[mem]]
+    exp_gv = torch.zeros_like(vel)
+    exp_gv[mem] = (2 * w[:, None] / (3 * cnt[:, None]))[hid[mem]] * (vel.detach()[mem] - vm.detach()[hid[mem]])
+    assert torch.allclose(pos.grad, exp_gp, rtol=1e-4, atol=1e-6 * exp_gp.abs().max().item())
+    assert torch.allclose(vel.grad, exp_gv, rtol=1e-4, atol=1e-6 * exp_gv.abs().max().item())
+
+
+def test_box_256cubed_full_parity(J):
+    spec = synth.BOX_256
+    pos, vel = synth.generate(spec, device="cuda")
+    pos_np = pos.cpu().numpy()
+    lab_ref = oracle.fof_labels(pos_np, spec.L, spec.b)
+    _, r, H = run_fof(J, pos_np, spec.L, spec.b, spec.min_size)
+    assert np.array_equal(r.label.cpu().numpy(), lab_ref)
+    check_groups(r, H, lab_ref, spec.min_size)
+    props_check(J, pos, vel, r, H, spec.L, lab_ref, spec.min_size)
