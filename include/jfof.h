@@ -87,6 +87,12 @@ int jfof_set_loop_budget(jfof_ctx *ctx, int64_t iterations);
 int jfof_trace_enable(jfof_ctx *ctx, int on);
 int jfof_trace_read(jfof_ctx *ctx, char *buf, size_t len, size_t *written);
 
+/* Dense-cell threshold: a cell with more than `threshold` particles (and at
+   most 65535) is linked through its sub-cells (see jfof_link); 0 disables
+   that path.  Default 64.  Labels do not depend on it; only speed does.
+   Takes effect at the next jfof_bin_cells. */
+int jfof_set_dense_threshold(jfof_ctx *ctx, int32_t threshold);
+
 /* ---------------------------------------------------------------------- */
 /* Grid choice (Sec. 2.2, Algorithm 2 "Grid setup").                        */
 /* The linked-cell grid has n cells per axis with cell side L/n >= 1.01 b,  */
@@ -111,11 +117,13 @@ typedef struct {
     int32_t brick;        /* cells per brick side (cell table is brick-major) */
     float L, b;           /* box side and linking length */
     uint32_t flags;       /* flags given to jfof_bin_cells */
+    int32_t dense_threshold; /* cells with more particles take the dense path (0 = off) */
     void *spos;           /* device float4[n]: positions in cell order; .w holds the
                              bits of the int32 original index */
     uint32_t *cell_start; /* device [n_cells_table + 1]: start of each cell in spos */
     int64_t n_cells_table;/* entries of the brick-major cell table */
-    void *scratch;        /* device scratch (>= 16 n bytes) reused by jfof_link */
+    void *workspace;      /* the workspace given to jfof_bin_cells; jfof_link uses
+                             the rest of it (union-find forest, dense-cell tables) */
 } jfof_cells;
 
 /* Bytes of workspace for jfof_bin_cells + jfof_link with N particles and
@@ -136,7 +144,11 @@ int jfof_bin_cells(jfof_ctx *ctx, const float *pos, int64_t N, float L, float b,
    d2 <= b*b with d2 = (dx*dx + dy*dy) + dz*dz in binary32 without FMA on
    minimum-image differences, lock-free union-find, and the raw label
    label[i] = smallest original index in i's component, in original order.
-   label: device int32 [N].  Sec. 2 steps (iii)-(v); Algorithm 2. */
+   Dense cells are split into sub-cells of side <= b/(1.02 sqrt 3): pairs in
+   one sub-cell are friends by geometry and are united without a test, and a
+   sub-cell pair is tested only until its first link (the components are
+   those of testing every pair).  label: device int32 [N].  Sec. 2 steps
+   (iii)-(v); Sec. 2.2; Algorithm 2. */
 int jfof_link(jfof_ctx *ctx, const jfof_cells *cells, int32_t *label);
 
 /* Bytes of workspace for jfof_groups with N particles. */

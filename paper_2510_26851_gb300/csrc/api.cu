@@ -68,10 +68,14 @@ size_t fof_layout(int64_t N, int n, FofBuffers *fb, void *base) {
     f.brick_start = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * size_t(n_bricks + 1)));
     f.cursor = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * size_t(n_bricks + 1)));
     f.scan_tmp = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * scan_tmp_words(n_bricks)));
-    // bin scatter buffer; reused by the link as parent[N] + rootmin[N]
-    size_t scratch = sizeof(float4) * size_t(N);
-    size_t link_need = sizeof(int) * (align_up(size_t(N), 64) + size_t(N));
-    f.tmp = reinterpret_cast<float4 *>(take(scratch > link_need ? scratch : link_need));
+    // bin scatter buffer; dense-cell staging; then the link's rootmin[N]
+    f.tmp = reinterpret_cast<float4 *>(take(sizeof(float4) * size_t(N)));
+    f.parent = reinterpret_cast<int *>(take(sizeof(int) * size_t(N)));
+    f.dense_id = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * size_t(cell_table_entries(n))));
+    int64_t D_cap = dense_cap(N);
+    f.dense_cells = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * size_t(D_cap)));
+    f.ndense = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t)));
+    f.sub_start = reinterpret_cast<uint16_t *>(take(sizeof(uint16_t) * size_t(D_cap) * (kSubMax + 1)));
     if (fb) *fb = f;
     return off;
 }
@@ -102,6 +106,7 @@ int jfof_create(jfof_ctx **ctx, int device, void *stream) {
     c->tracer = nullptr;
     c->stream = reinterpret_cast<cudaStream_t>(stream);
     c->loop_budget = kDefaultLoopBudget;
+    c->dense_threshold = kDefaultDenseThreshold;
     if (cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess) {
         delete c;
         return JFOF_ECUDA;
@@ -188,7 +193,8 @@ int jfof_bin_cells(jfof_ctx *ctx, const float *pos, int64_t N, float L, float b,
     if (ws_bytes < need) return JFOF_ENOMEM;
     cudaSetDevice(ctx->device);
     CtxScope scope(ctx);
-    launch_bin_cells(pos, N, L, n, (flags & JFOF_WRAP) != 0, fb, ctx->dev(), ctx->stream);
+    LinkParams lp = make_link_params(N, L, b, n, ctx->dense_threshold);
+    launch_bin_cells(pos, N, L, n, (flags & JFOF_WRAP) != 0, lp, fb, ctx->dev(), ctx->stream);
     jfof_cells c;
     c.n = N;
     c.n_axis = n;
@@ -196,23 +202,35 @@ int jfof_bin_cells(jfof_ctx *ctx, const float *pos, int64_t N, float L, float b,
     c.L = L;
     c.b = b;
     c.flags = flags;
+    c.dense_threshold = lp.T;
     c.spos = fb.spos;
     c.cell_start = fb.cell_start;
     c.n_cells_table = cell_table_entries(n);
-    c.scratch = fb.tmp;
+    c.workspace = ws;
     *cells = c;
     return launch_status();
 }
 
 int jfof_link(jfof_ctx *ctx, const jfof_cells *cells, int32_t *label) {
-    if (!ctx || !cells || !label || !cells->spos || !cells->cell_start || !cells->scratch) return JFOF_EINVAL;
+    if (!ctx || !cells || !label || !cells->spos || !cells->cell_start || !cells->workspace) return JFOF_EINVAL;
     int e = check_box(cells->n, cells->L, cells->b);
     if (e) return e;
     if (cells->n_axis < 1 || cells->n_axis == 2 || cells->n_axis > max_cells(cells->L, cells->b)) return JFOF_EINVAL;
+    FofBuffers fb;
+    fof_layout(cells->n, cells->n_axis, &fb, cells->workspace);
+    if (fb.spos != cells->spos || fb.cell_start != cells->cell_start) return JFOF_EINVAL;
+    LinkParams lp = make_link_params(cells->n, cells->L, cells->b, cells->n_axis, cells->dense_threshold);
+    if (lp.T != cells->dense_threshold) return JFOF_EINVAL;
     cudaSetDevice(ctx->device);
     CtxScope scope(ctx);
-    launch_link(*cells, label, ctx->dev(), ctx->stream);
+    launch_link(*cells, fb, lp, label, ctx->dev(), ctx->stream);
     return launch_status();
+}
+
+int jfof_set_dense_threshold(jfof_ctx *ctx, int32_t threshold) {
+    if (!ctx || threshold < 0) return JFOF_EINVAL;
+    ctx->dense_threshold = threshold;
+    return JFOF_OK;
 }
 
 int jfof_groups_bytes(int64_t N, size_t *bytes) {

@@ -247,6 +247,7 @@ struct jfof_ctx {
     int *d_status;       // device status word
     int *h_status;       // pinned host mirror
     int64_t loop_budget;
+    int dense_threshold;
     jfof::DevStatus dev() const { return jfof::DevStatus{d_status, loop_budget}; }
 };
 

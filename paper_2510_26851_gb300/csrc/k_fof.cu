@@ -1,12 +1,28 @@
 // k_fof.cu -- a1-a6 of the hot path on sm_103a: wrap, cell binning, two-level
-// counting sort by cell, the 27-cell neighbour scan fused with lock-free
-// union-find, and the raw labels (smallest original index per component).
+// counting sort by cell, the neighbour scan fused with lock-free union-find,
+// and the raw labels (smallest original index per component).
 //
-// Layout in HBM (all in the caller's workspace):
-//   tmp   float4[N]   particles grouped by brick (16^3 cells), scatter order
-//   spos  float4[N]   particles sorted by cell (brick-major), .w = original index
+// Layout in HBM (all in the caller's workspace, see fof_layout):
+//   tmp        float4[N]  particles grouped by brick (16^3 cells); later the
+//                         staging area of the dense-cell sort, then rootmin
+//   spos       float4[N]  particles sorted by cell (brick-major); .w = original
+//                         index; inside a dense cell also sorted by sub-cell
 //   cell_start u32[nb^3 * 4096 + 1]   brick-major cell table
-//   parent i32[N], rootmin i32[N]     union-find forest over sorted slots (reuse tmp)
+//   parent     i32[N]     union-find forest over sorted slots (parent <= slot)
+//   dense_id   u32[cells] id of each dense cell (written only for them)
+//   dense_cells u32[D_cap], sub_start u16[D_cap][kSubMax+1]
+//
+// Linking in two regimes.  Cells of side s >= 1.01 b guarantee that friends
+// are in the same or adjacent cells (Sec. 2.2, Algorithm 2, with the grid
+// reading of the design notes).  A cell holding more than T particles is
+// "dense": its particles are re-sorted by sub-cells of side s_f = s/k with
+// sqrt(3) s_f <= b/1.02, so every pair inside one sub-cell is within b under
+// the binary32 predicate (the 2% margin dwarfs the ~1e-6 b rounding of the
+// cell assignment and of d2); such pairs are linked without being tested.
+// Friends then differ by at most 2 sub-cells per axis.  Two sub-cells are
+// joined as soon as one tested pair links, and a sub-cell whose root already
+// equals the other side's root is skipped.  Every other pair is tested with
+// the exact predicate, so the components equal those of testing all pairs.
 #include "jfof_internal.cuh"
 #include "k_fof.cuh"
 
@@ -60,14 +76,23 @@ __global__ void __launch_bounds__(256) bin_scatter_kernel(const float *__restric
 }
 
 // Pass 3: one CTA per brick (persistent loop): shared-memory counting sort of
-// the brick's particles by local cell; writes the brick's 4096 cell starts.
+// the brick's particles by local cell; writes the brick's 4096 cell starts and
+// registers the dense cells (more than T particles).
 constexpr int kSortThreads = 512;
+
+struct DenseReg {
+    int T;                    // 0: no dense path
+    uint32_t *dense_id;       // [cell table]
+    uint32_t *dense_cells;    // [D_cap]
+    uint32_t *ndense;         // counter
+    int64_t D_cap;
+};
 
 __global__ void __launch_bounds__(kSortThreads) brick_sort_kernel(const float4 *__restrict__ tmp,
                                                                   const uint32_t *__restrict__ brick_start,
                                                                   int64_t n_bricks, BinGeom g,
                                                                   float4 *__restrict__ spos,
-                                                                  uint32_t *__restrict__ cell_start) {
+                                                                  uint32_t *__restrict__ cell_start, DenseReg dr) {
     __shared__ uint32_t hist[kBrickCells];
     __shared__ uint32_t warps[kSortThreads / 32];
     constexpr int per = kBrickCells / kSortThreads;  // 8
@@ -95,9 +120,15 @@ __global__ void __launch_bounds__(kSortThreads) brick_sort_kernel(const float4 *
         uint64_t tbase = uint64_t(brick) * kBrickCells;
 #pragma unroll
         for (int k = 0; k < per; ++k) {
+            uint64_t gidx = tbase + threadIdx.x * per + k;
             hist[threadIdx.x * per + k] = pre;
-            cell_start[tbase + threadIdx.x * per + k] = bs + pre;
+            cell_start[gidx] = bs + pre;
             pre += v[k];
+            if (dr.T > 0 && v[k] > uint32_t(dr.T) && v[k] <= kDenseMaxM) {
+                uint32_t id = atomicAdd(dr.ndense, 1u);
+                dr.dense_id[gidx] = id;
+                if (int64_t(id) < dr.D_cap) dr.dense_cells[id] = uint32_t(gidx);
+            }
         }
         __syncthreads();
         for (uint32_t e = bs + threadIdx.x; e < be; e += kSortThreads) {
@@ -114,77 +145,373 @@ __global__ void __launch_bounds__(kSortThreads) brick_sort_kernel(const float4 *
 
 __global__ void set_u32_kernel(uint32_t *p, uint32_t v) { *p = v; }
 
-void launch_bin_cells(const float *pos, int64_t N, float L, int n, bool wrap, const FofBuffers &fb,
-                      const DevStatus &st, cudaStream_t s) {
+void launch_bin_cells(const float *pos, int64_t N, float L, int n, bool wrap, const LinkParams &lp,
+                      const FofBuffers &fb, const DevStatus &st, cudaStream_t s) {
     BinGeom g{L, float(double(n) / double(L)), n, bricks_per_axis(n), wrap};
     int64_t n_bricks = int64_t(g.nb) * g.nb * g.nb;
     cudaMemsetAsync(fb.brick_count, 0, sizeof(uint32_t) * size_t(n_bricks), s);
+    cudaMemsetAsync(fb.ndense, 0, sizeof(uint32_t), s);
     {
         JFOF_TRACE("bin_count", s);
         bin_count_kernel<<<grid_for(N, 256), 256, 0, s>>>(pos, N, g, fb.brick_count, st);
     }
-    { JFOF_TRACE("scan", s); scan_exclusive(LoadU32{fb.brick_count}, n_bricks, fb.brick_start, fb.scan_tmp, s); }
+    {
+        JFOF_TRACE("scan", s);
+        scan_exclusive(LoadU32{fb.brick_count}, n_bricks, fb.brick_start, fb.scan_tmp, s);
+    }
     cudaMemcpyAsync(fb.cursor, fb.brick_start, sizeof(uint32_t) * size_t(n_bricks), cudaMemcpyDeviceToDevice, s);
     {
         JFOF_TRACE("bin_scatter", s);
         bin_scatter_kernel<<<grid_for(N, 256), 256, 0, s>>>(pos, N, g, fb.cursor, fb.tmp, st);
     }
+    DenseReg dr{lp.T, fb.dense_id, fb.dense_cells, fb.ndense, lp.D_cap};
     {
         JFOF_TRACE("brick_sort", s);
         brick_sort_kernel<<<grid_for(n_bricks * kSortThreads, kSortThreads, 4), kSortThreads, 0, s>>>(
-            fb.tmp, fb.brick_start, n_bricks, g, fb.spos, fb.cell_start);
+            fb.tmp, fb.brick_start, n_bricks, g, fb.spos, fb.cell_start, dr);
     }
     set_u32_kernel<<<1, 1, 0, s>>>(fb.cell_start + n_bricks * kBrickCells, uint32_t(N));
 }
 
 // ---------------------------------------------------------------------------
-// a4+a5: neighbour scan fused with union-find.  One thread per sorted slot s:
-// pairs (s, j) with j > s inside its own cell, and every particle of the 13
-// "forward" neighbour cells (offsets whose first non-zero component of
-// (dz, dy, dx) is positive), so each unordered adjacent cell pair is visited
-// once.  The predicate is symmetric bit for bit (fl(a-b) = -fl(b-a) and the
-// minimum-image correction is sign-symmetric), so testing (s, j) once from
-// either side gives the same answer.
+// Link geometry and helpers.
 struct LinkGeom {
-    float L, hL, b2, inv_cell;
-    int n, nb;
+    float L, hL, b2, inv_cell, inv_fine, cell_side, gap2;
+    int n, nb, k, k3, T;
+    int64_t D_cap;
 };
 
-__constant__ int8_t c_fwd[13][3] = {{1, 0, 0},  {-1, 1, 0}, {0, 1, 0},  {1, 1, 0},  {-1, -1, 1},
-                                    {0, -1, 1}, {1, -1, 1}, {-1, 0, 1}, {0, 0, 1},  {1, 0, 1},
-                                    {-1, 1, 1}, {0, 1, 1},  {1, 1, 1}};
+// 13 "forward" cell offsets (first non-zero of (dz, dy, dx) positive) followed
+// by their negatives: each unordered pair of adjacent cells is one forward
+// offset away from exactly one of its two cells (n >= 3).
+__constant__ int8_t c_nb26[26][3] = {
+    {1, 0, 0},   {-1, 1, 0}, {0, 1, 0},   {1, 1, 0},   {-1, -1, 1}, {0, -1, 1},  {1, -1, 1},
+    {-1, 0, 1},  {0, 0, 1},  {1, 0, 1},   {-1, 1, 1},  {0, 1, 1},   {1, 1, 1},   {-1, 0, 0},
+    {1, -1, 0},  {0, -1, 0}, {-1, -1, 0}, {1, 1, -1},  {0, 1, -1},  {-1, 1, -1}, {1, 0, -1},
+    {0, 0, -1},  {-1, 0, -1}, {1, -1, -1}, {0, -1, -1}, {-1, -1, -1}};
+
+// 62 forward sub-cell offsets of the 5x5x5 stencil (first non-zero of
+// (dz, dy, dx) positive); filled on the host at first use.
+__constant__ int8_t c_sub62[62][3];
+
+__device__ __forceinline__ void decode_cell(uint32_t gidx, int nb, int &cx, int &cy, int &cz) {
+    uint32_t brick = gidx >> 12, local = gidx & 4095u;
+    uint32_t bx = brick % uint32_t(nb), by = (brick / uint32_t(nb)) % uint32_t(nb), bz = brick / (uint32_t(nb) * nb);
+    cx = int(bx * 16 + (local & 15u));
+    cy = int(by * 16 + ((local >> 4) & 15u));
+    cz = int(bz * 16 + (local >> 8));
+}
+
+__device__ __forceinline__ int wrapc(int c, int n) { return c < 0 ? c + n : (c >= n ? c - n : c); }
+
+// Sub-cell coordinate of x inside cell c (fine index clamped to the cell).
+__device__ __forceinline__ int sub_coord(float x, float inv_fine, int c, int k) {
+    int f = __float2int_rd(__fmul_rn(x, inv_fine)) - c * k;
+    f = f < 0 ? 0 : f;
+    f = f > k - 1 ? k - 1 : f;
+    return f;
+}
+
+__device__ __forceinline__ bool is_dense(uint32_t m, uint64_t gidx, const LinkGeom &g, const uint32_t *dense_id) {
+    return g.T > 0 && m > uint32_t(g.T) && m <= kDenseMaxM && int64_t(dense_id[gidx]) < g.D_cap;
+}
+
+__device__ __forceinline__ bool linked(float4 p, float4 q, const LinkGeom &g) {
+    return pair_d2(p, q, g.L, g.hL) <= g.b2;
+}
 
 __global__ void iota_kernel(int *__restrict__ p, int64_t N) {
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x)
         p[i] = int(i);
 }
 
-__device__ __forceinline__ void scan_range(const float4 *__restrict__ spos, float4 p, int s, uint32_t a, uint32_t e,
-                                           const LinkGeom &g, int *parent, const DevStatus &st) {
-    for (uint32_t j = a; j < e; ++j) {
-        float4 q = spos[j];
-        if (pair_d2(p, q, g.L, g.hL) <= g.b2) uf_unite(parent, s, int(j), st);
+// ---------------------------------------------------------------------------
+// Dense cells: one warp per dense cell.  Counting sort of the cell's particles
+// by sub-cell (staged through tmp), the sub-cell table, then a shared-memory
+// union-find over the cell's sub-cells (a sub-cell is one node: its members
+// are friends), and finally parent[slot] = first slot of the slot's local
+// component.
+constexpr int kDenseWarps = 8;
+
+// Path halving in shared memory (each write stores an ancestor of a non-root,
+// so concurrent finds and the CAS hook stay correct, as in uf_find).
+__device__ __forceinline__ int lfind(volatile int *lp, int x) {
+    while (true) {
+        int p = lp[x];
+        if (p == x) return x;
+        int gp = lp[p];
+        if (gp == p) return p;
+        lp[x] = gp;
+        x = gp;
     }
 }
 
-__global__ void __launch_bounds__(256) link_kernel(const float4 *__restrict__ spos,
-                                                   const uint32_t *__restrict__ cell_start, int64_t N, LinkGeom g,
-                                                   int *parent, DevStatus st) {
+__device__ __forceinline__ void lunite(int *lp, int a, int b) {
+    for (int it = 0; it < 4 * kSubMax; ++it) {
+        int ra = lfind(lp, a), rb = lfind(lp, b);
+        if (ra == rb) return;
+        if (ra < rb) {
+            int t = ra;
+            ra = rb;
+            rb = t;
+        }
+        if (atomicCAS(&lp[ra], ra, rb) == ra) return;
+    }
+}
+
+__global__ void __launch_bounds__(32 * kDenseWarps) dense_cells_kernel(float4 *__restrict__ spos,
+                                                                       float4 *__restrict__ stage,
+                                                                       const uint32_t *__restrict__ cell_start,
+                                                                       const uint32_t *__restrict__ dense_cells,
+                                                                       const uint32_t *__restrict__ ndense,
+                                                                       uint16_t *__restrict__ sub_start,
+                                                                       int *__restrict__ parent, LinkGeom g) {
+    __shared__ int sh_cnt[kDenseWarps][kSubMax + 1];
+    __shared__ uint16_t sh_ss[kDenseWarps][kSubMax + 2];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int *cnt = sh_cnt[w];
+    uint16_t *ss = sh_ss[w];
+    int64_t D = *ndense;
+    if (D > g.D_cap) D = g.D_cap;
+    const int k = g.k, k3 = g.k3;
+    for (int64_t d = int64_t(blockIdx.x) * kDenseWarps + w; d < D; d += int64_t(gridDim.x) * kDenseWarps) {
+        uint32_t gidx = dense_cells[d];
+        uint32_t start = cell_start[gidx];
+        int m = int(cell_start[gidx + 1] - start);
+        int cx, cy, cz;
+        decode_cell(gidx, g.nb, cx, cy, cz);
+        for (int key = lane; key < k3; key += 32) cnt[key] = 0;
+        __syncwarp();
+        for (int t = lane; t < m; t += 32) {
+            float4 q = spos[start + t];
+            stage[start + t] = q;
+            int key = sub_coord(q.x, g.inv_fine, cx, k) + k * (sub_coord(q.y, g.inv_fine, cy, k) +
+                                                               k * sub_coord(q.z, g.inv_fine, cz, k));
+            atomicAdd(&cnt[key], 1);
+        }
+        __syncwarp();
+        // exclusive scan of the k3 counts: lane owns a contiguous chunk
+        const int chunk = (k3 + 31) / 32;
+        int lo = lane * chunk, hi = min(lo + chunk, k3);
+        int sum = 0;
+        for (int key = lo; key < hi; ++key) sum += cnt[key];
+        int x = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        int pre = x - sum;
+        uint16_t *tab = sub_start + d * (kSubMax + 1);
+        for (int key = lo; key < hi; ++key) {
+            int c = cnt[key];
+            ss[key] = uint16_t(pre);
+            tab[key] = uint16_t(pre);
+            cnt[key] = pre;
+            pre += c;
+        }
+        if (lane == 0) {
+            ss[k3] = uint16_t(m);
+            tab[k3] = uint16_t(m);
+        }
+        __syncwarp();
+        for (int t = lane; t < m; t += 32) {
+            float4 q = stage[start + t];
+            int key = sub_coord(q.x, g.inv_fine, cx, k) + k * (sub_coord(q.y, g.inv_fine, cy, k) +
+                                                               k * sub_coord(q.z, g.inv_fine, cz, k));
+            int r = atomicAdd(&cnt[key], 1);
+            spos[start + r] = q;
+        }
+        __syncwarp();
+        // local union-find over sub-cells (cnt reused as the forest)
+        for (int key = lane; key < k3; key += 32) cnt[key] = key;
+        __syncwarp();
+        for (int F = lane; F < k3; F += 32) {
+            int f0 = ss[F], f1 = ss[F + 1];
+            if (f0 == f1) continue;
+            int fx = F % k, fy = (F / k) % k, fz = F / (k * k);
+            for (int o = 0; o < 62; ++o) {
+                int gx = fx + c_sub62[o][0], gy = fy + c_sub62[o][1], gz = fz + c_sub62[o][2];
+                if (gx < 0 || gx >= k || gy < 0 || gy >= k || gz < 0 || gz >= k) continue;
+                int G = gx + k * (gy + k * gz);
+                int g0 = ss[G], g1 = ss[G + 1];
+                if (g0 == g1) continue;
+                if (lfind(cnt, F) == lfind(cnt, G)) continue;
+                bool done = false;
+                for (int a = f0; a < f1 && !done; ++a) {
+                    float4 p = spos[start + a];
+                    for (int c = g0; c < g1; ++c) {
+                        if (linked(p, spos[start + c], g)) {
+                            lunite(cnt, F, G);
+                            done = true;
+                            break;
+                        }
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        for (int t = lane; t < m; t += 32) {
+            float4 q = spos[start + t];
+            int key = sub_coord(q.x, g.inv_fine, cx, k) + k * (sub_coord(q.y, g.inv_fine, cy, k) +
+                                                               k * sub_coord(q.z, g.inv_fine, cz, k));
+            parent[start + t] = int(start) + ss[lfind(cnt, key)];
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Sparse probes: one thread per particle of a sparse cell.  Pairs with later
+// particles of its own cell; with every particle of a sparse forward
+// neighbour cell (skipped when the particle is farther than b from that
+// cell); and with the sub-cells of any dense neighbour cell within reach.
+__global__ void __launch_bounds__(256) probe_kernel(const float4 *__restrict__ spos,
+                                                    const uint32_t *__restrict__ cell_start,
+                                                    const uint32_t *__restrict__ dense_id,
+                                                    const uint16_t *__restrict__ sub_start, int64_t N, LinkGeom g,
+                                                    int *parent, DevStatus st) {
     for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < N; s += int64_t(gridDim.x) * blockDim.x) {
         float4 p = spos[s];
         int cx = cell_coord(p.x, g.inv_cell, g.n), cy = cell_coord(p.y, g.inv_cell, g.n),
             cz = cell_coord(p.z, g.inv_cell, g.n);
         uint64_t own = cell_table_index(cx, cy, cz, g.nb);
-        scan_range(spos, p, int(s), uint32_t(s) + 1, cell_start[own + 1], g, parent, st);
+        uint32_t a0 = cell_start[own], a1 = cell_start[own + 1];
+        if (is_dense(a1 - a0, own, g, dense_id)) continue;
+        for (uint32_t j = uint32_t(s) + 1; j < a1; ++j)
+            if (linked(p, spos[j], g)) uf_unite(parent, int(s), int(j), st);
         if (g.n < 3) continue;
+        // gaps to the lower / upper faces of the own cell (for pruning)
+        float lo_gap[3], hi_gap[3];
+        {
+            float pc[3] = {p.x, p.y, p.z};
+            int cc[3] = {cx, cy, cz};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                lo_gap[a] = pc[a] - float(cc[a]) * g.cell_side;
+                hi_gap[a] = float(cc[a] + 1) * g.cell_side - pc[a];
+            }
+        }
+        int lf[3] = {-1, -1, -1};
 #pragma unroll 1
-        for (int k = 0; k < 13; ++k) {
-            int nx = cx + c_fwd[k][0], ny = cy + c_fwd[k][1], nz = cz + c_fwd[k][2];
-            nx = nx < 0 ? nx + g.n : (nx >= g.n ? nx - g.n : nx);
-            ny = ny < 0 ? ny + g.n : (ny >= g.n ? ny - g.n : ny);
-            nz = nz < 0 ? nz + g.n : (nz >= g.n ? nz - g.n : nz);
-            uint64_t c = cell_table_index(nx, ny, nz, g.nb);
-            scan_range(spos, p, int(s), cell_start[c], cell_start[c + 1], g, parent, st);
+        for (int o = 0; o < 26; ++o) {
+            int ox = c_nb26[o][0], oy = c_nb26[o][1], oz = c_nb26[o][2];
+            float gx = ox > 0 ? hi_gap[0] : (ox < 0 ? lo_gap[0] : 0.f);
+            float gy = oy > 0 ? hi_gap[1] : (oy < 0 ? lo_gap[1] : 0.f);
+            float gz = oz > 0 ? hi_gap[2] : (oz < 0 ? lo_gap[2] : 0.f);
+            gx = fmaxf(gx, 0.f);
+            gy = fmaxf(gy, 0.f);
+            gz = fmaxf(gz, 0.f);
+            if (gx * gx + gy * gy + gz * gz > g.gap2) continue;
+            int nx = wrapc(cx + ox, g.n), ny = wrapc(cy + oy, g.n), nz = wrapc(cz + oz, g.n);
+            uint64_t nb = cell_table_index(nx, ny, nz, g.nb);
+            uint32_t b0 = cell_start[nb], b1 = cell_start[nb + 1];
+            if (b0 == b1) continue;
+            if (!is_dense(b1 - b0, nb, g, dense_id)) {
+                if (o >= 13) continue;  // the other cell's forward pass covers it
+                for (uint32_t j = b0; j < b1; ++j)
+                    if (linked(p, spos[j], g)) uf_unite(parent, int(s), int(j), st);
+                continue;
+            }
+            if (lf[0] < 0) {
+                lf[0] = sub_coord(p.x, g.inv_fine, cx, g.k);
+                lf[1] = sub_coord(p.y, g.inv_fine, cy, g.k);
+                lf[2] = sub_coord(p.z, g.inv_fine, cz, g.k);
+            }
+            int off[3] = {ox, oy, oz}, lo[3], hi[3];
+            bool empty = false;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                int c = lf[a] - off[a] * g.k;
+                lo[a] = max(c - 2, 0);
+                hi[a] = min(c + 2, g.k - 1);
+                empty |= lo[a] > hi[a];
+            }
+            if (empty) continue;
+            const uint16_t *tab = sub_start + int64_t(dense_id[nb]) * (kSubMax + 1);
+            for (int zz = lo[2]; zz <= hi[2]; ++zz)
+                for (int yy = lo[1]; yy <= hi[1]; ++yy)
+                    for (int xx = lo[0]; xx <= hi[0]; ++xx) {
+                        int G = xx + g.k * (yy + g.k * zz);
+                        uint32_t c0 = tab[G], c1 = tab[G + 1];
+                        if (c0 == c1) continue;
+                        if (uf_find(parent, int(s)) == uf_find(parent, int(b0 + c0))) continue;
+                        for (uint32_t c = c0; c < c1; ++c)
+                            if (linked(p, spos[b0 + c], g)) {
+                                uf_unite(parent, int(s), int(b0 + c), st);
+                                break;
+                            }
+                    }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Dense-dense neighbour pairs: one warp per (dense cell, forward offset) whose
+// neighbour is also dense.  Sub-cells of A within reach of B against the
+// sub-cells of B within reach of each: skipped when already in one
+// component, else tested until the first link.
+__global__ void __launch_bounds__(256) dense_pairs_kernel(const float4 *__restrict__ spos,
+                                                          const uint32_t *__restrict__ cell_start,
+                                                          const uint32_t *__restrict__ dense_cells,
+                                                          const uint32_t *__restrict__ ndense,
+                                                          const uint32_t *__restrict__ dense_id,
+                                                          const uint16_t *__restrict__ sub_start, LinkGeom g,
+                                                          int *parent, DevStatus st) {
+    const int lane = threadIdx.x & 31;
+    int64_t D = *ndense;
+    if (D > g.D_cap) D = g.D_cap;
+    const int k = g.k;
+    int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t task = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; task < D * 13; task += nw) {
+        int64_t d = task / 13;
+        int o = int(task % 13);
+        uint32_t ga = dense_cells[d];
+        int cx, cy, cz;
+        decode_cell(ga, g.nb, cx, cy, cz);
+        int off[3] = {c_nb26[o][0], c_nb26[o][1], c_nb26[o][2]};
+        uint64_t gb = cell_table_index(wrapc(cx + off[0], g.n), wrapc(cy + off[1], g.n), wrapc(cz + off[2], g.n), g.nb);
+        uint32_t b0 = cell_start[gb], b1 = cell_start[gb + 1];
+        if (!is_dense(b1 - b0, gb, g, dense_id)) continue;
+        uint32_t a0 = cell_start[ga];
+        const uint16_t *ta = sub_start + d * (kSubMax + 1);
+        const uint16_t *tb = sub_start + int64_t(dense_id[gb]) * (kSubMax + 1);
+        int flo[3], fn[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            flo[a] = off[a] > 0 ? k - 2 : 0;
+            fn[a] = off[a] != 0 ? 2 : k;
+        }
+        int nF = fn[0] * fn[1] * fn[2];
+        for (int f = lane; f < nF; f += 32) {
+            int fx = flo[0] + f % fn[0], fy = flo[1] + (f / fn[0]) % fn[1], fz = flo[2] + f / (fn[0] * fn[1]);
+            int F = fx + k * (fy + k * fz);
+            uint32_t f0 = ta[F], f1 = ta[F + 1];
+            if (f0 == f1) continue;
+            int fc[3] = {fx, fy, fz}, lo[3], hi[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                int c = fc[a] - off[a] * k;
+                lo[a] = max(c - 2, 0);
+                hi[a] = min(c + 2, k - 1);
+            }
+            for (int zz = lo[2]; zz <= hi[2]; ++zz)
+                for (int yy = lo[1]; yy <= hi[1]; ++yy)
+                    for (int xx = lo[0]; xx <= hi[0]; ++xx) {
+                        int G = xx + k * (yy + k * zz);
+                        uint32_t c0 = tb[G], c1 = tb[G + 1];
+                        if (c0 == c1) continue;
+                        if (uf_find(parent, int(a0 + f0)) == uf_find(parent, int(b0 + c0))) continue;
+                        bool done = false;
+                        for (uint32_t a = f0; a < f1 && !done; ++a) {
+                            float4 p = spos[a0 + a];
+                            for (uint32_t c = c0; c < c1; ++c)
+                                if (linked(p, spos[b0 + c], g)) {
+                                    uf_unite(parent, int(a0 + a), int(b0 + c), st);
+                                    done = true;
+                                    break;
+                                }
+                        }
+                    }
         }
     }
 }
@@ -211,29 +538,81 @@ __global__ void __launch_bounds__(256) finalize_labels_kernel(const float4 *__re
     }
 }
 
-void launch_link(const jfof_cells &c, int32_t *label, const DevStatus &st, cudaStream_t s) {
+// ---------------------------------------------------------------------------
+static bool g_sub62_ready = false;
+
+static void ensure_sub_offsets() {
+    if (g_sub62_ready) return;
+    int8_t t[62][3];
+    int c = 0;
+    for (int dz = -2; dz <= 2; ++dz)
+        for (int dy = -2; dy <= 2; ++dy)
+            for (int dx = -2; dx <= 2; ++dx) {
+                bool fwd = dz > 0 || (dz == 0 && (dy > 0 || (dy == 0 && dx > 0)));
+                if (!fwd) continue;
+                t[c][0] = int8_t(dx);
+                t[c][1] = int8_t(dy);
+                t[c][2] = int8_t(dz);
+                ++c;
+            }
+    cudaMemcpyToSymbol(c_sub62, t, sizeof(t));
+    g_sub62_ready = true;
+}
+
+LinkParams make_link_params(int64_t N, float L, float b, int n, int T) {
+    LinkParams lp{};
+    double s = double(L) / n;
+    int k = int(std::ceil(s * std::sqrt(3.0) * 1.02 / double(b)));
+    if (k < 1) k = 1;
+    double sf = s / k;
+    double eps = 4.0 * double(L) * std::ldexp(1.0, -24);
+    bool ok = T > 0 && n >= 5 && k <= kSubSide && std::sqrt(3.0) * (sf + 2 * eps) <= double(b) * (1 - 1e-4) &&
+              (double(b) + 2 * eps) / sf < 2.0;
+    lp.T = ok ? T : 0;
+    lp.k = k;
+    lp.inv_fine = float(double(n) * k / double(L));
+    lp.D_cap = ok ? N / 256 + 1024 : 0;
+    return lp;
+}
+
+void launch_link(const jfof_cells &c, const FofBuffers &fb, const LinkParams &lp, int32_t *label,
+                 const DevStatus &st, cudaStream_t s) {
     int64_t N = c.n;
-    int *parent = reinterpret_cast<int *>(c.scratch);
-    int *rootmin = parent + align_up(size_t(N), 64);
+    ensure_sub_offsets();
+    float b2 = host_mul(c.b, c.b);
+    double gap = 1.02 * double(c.b);
+    LinkGeom g{c.L, 0.5f * c.L, b2, float(double(c.n_axis) / double(c.L)), lp.inv_fine,
+               float(double(c.L) / c.n_axis), float(gap * gap), c.n_axis, bricks_per_axis(c.n_axis), lp.k,
+               lp.k * lp.k * lp.k, lp.T, lp.D_cap};
     const float4 *spos = reinterpret_cast<const float4 *>(c.spos);
-    LinkGeom g{c.L, 0.5f * c.L, host_mul(c.b, c.b), float(double(c.n_axis) / double(c.L)), c.n_axis,
-               bricks_per_axis(c.n_axis)};
     {
         JFOF_TRACE("link_init", s);
-        iota_kernel<<<grid_for(N, 256), 256, 0, s>>>(parent, N);
+        iota_kernel<<<grid_for(N, 256), 256, 0, s>>>(fb.parent, N);
+    }
+    if (lp.T > 0) {
+        JFOF_TRACE("dense_cells", s);
+        dense_cells_kernel<<<grid_for(lp.D_cap * 32, 32 * kDenseWarps, 4), 32 * kDenseWarps, 0, s>>>(
+            fb.spos, fb.tmp, c.cell_start, fb.dense_cells, fb.ndense, fb.sub_start, fb.parent, g);
     }
     {
         JFOF_TRACE("link", s);
-        link_kernel<<<grid_for(N, 256), 256, 0, s>>>(spos, c.cell_start, N, g, parent, st);
+        probe_kernel<<<grid_for(N, 256), 256, 0, s>>>(spos, c.cell_start, fb.dense_id, fb.sub_start, N, g,
+                                                       fb.parent, st);
     }
+    if (lp.T > 0) {
+        JFOF_TRACE("dense_pairs", s);
+        dense_pairs_kernel<<<grid_for(lp.D_cap * 13 * 32, 256, 8), 256, 0, s>>>(
+            spos, c.cell_start, fb.dense_cells, fb.ndense, fb.dense_id, fb.sub_start, g, fb.parent, st);
+    }
+    int *rootmin = reinterpret_cast<int *>(fb.tmp);
     cudaMemsetAsync(rootmin, 0x7f, sizeof(int) * size_t(N), s);
     {
         JFOF_TRACE("finalize_roots", s);
-        finalize_roots_kernel<<<grid_for(N, 256), 256, 0, s>>>(spos, N, parent, rootmin);
+        finalize_roots_kernel<<<grid_for(N, 256), 256, 0, s>>>(spos, N, fb.parent, rootmin);
     }
     {
         JFOF_TRACE("finalize_labels", s);
-        finalize_labels_kernel<<<grid_for(N, 256), 256, 0, s>>>(spos, N, parent, rootmin, label);
+        finalize_labels_kernel<<<grid_for(N, 256), 256, 0, s>>>(spos, N, fb.parent, rootmin, label);
     }
 }
 

@@ -1,14 +1,25 @@
 // k_fof.cuh -- host-side launchers of the FoF kernels (internal).
 #pragma once
+#include <cmath>
+
 #include "jfof_internal.cuh"
 
 namespace jfof {
+
+// Dense-cell path: sub-cells per cell side (at most), their count, and the
+// largest cell it takes (sub-cell offsets are stored as uint16).
+constexpr int kSubSide = 9;
+constexpr int kSubMax = kSubSide * kSubSide * kSubSide;  // 729
+constexpr uint32_t kDenseMaxM = 65535;
+constexpr int kDefaultDenseThreshold = 64;
 
 // One IEEE binary32 multiply on the host (b*b for the link threshold).
 inline float host_mul(float a, float b) {
     volatile float r = a * b;
     return r;
 }
+
+inline int64_t dense_cap(int64_t N) { return N / 256 + 1024; }
 
 // Views into the bin/link workspace.
 struct FofBuffers {
@@ -18,13 +29,28 @@ struct FofBuffers {
     uint32_t *brick_start;
     uint32_t *cursor;
     uint32_t *scan_tmp;
-    float4 *tmp;  // also the link scratch (parent, rootmin)
+    float4 *tmp;           // bin scatter; dense-cell staging; then rootmin
+    int *parent;           // [N]
+    uint32_t *dense_id;    // [cell table]
+    uint32_t *dense_cells; // [D_cap]
+    uint32_t *ndense;      // [1]
+    uint16_t *sub_start;   // [D_cap][kSubMax + 1]
+};
+
+// Dense-path parameters derived on the host from (N, L, b, n, T).
+struct LinkParams {
+    int T;          // dense threshold actually used (0 = dense path off)
+    int k;          // sub-cells per cell side
+    float inv_fine; // f32(n k / L)
+    int64_t D_cap;  // dense cells with a sub-cell table
 };
 
 size_t fof_layout(int64_t N, int n, FofBuffers *fb, void *base);
-void launch_bin_cells(const float *pos, int64_t N, float L, int n, bool wrap, const FofBuffers &fb,
-                      const DevStatus &st, cudaStream_t s);
-void launch_link(const jfof_cells &c, int32_t *label, const DevStatus &st, cudaStream_t s);
+LinkParams make_link_params(int64_t N, float L, float b, int n, int T);
+void launch_bin_cells(const float *pos, int64_t N, float L, int n, bool wrap, const LinkParams &lp,
+                      const FofBuffers &fb, const DevStatus &st, cudaStream_t s);
+void launch_link(const jfof_cells &c, const FofBuffers &fb, const LinkParams &lp, int32_t *label,
+                 const DevStatus &st, cudaStream_t s);
 
 // Groups.
 struct GroupBuffers {

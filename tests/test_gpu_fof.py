@@ -86,6 +86,22 @@ def test_labels_invariant_across_grids(J, seed):
         assert np.array_equal(r.label.cpu().numpy(), lab_ref), n
 
 
+@pytest.mark.parametrize("boost", [1.0, 2.5])
+def test_labels_invariant_across_dense_thresholds(J, boost):
+    # threshold 0 turns the sub-cell path off; 1 sends almost every cell through it
+    spec = synth.BoxSpec("t", 300_000, 67.0, synth.linking_length(67.0, 300_000) * boost, 1500, 0.6, 9)
+    pos, _ = synth.generate(spec, device="cuda", velocities=False)
+    pos_np = pos.cpu().numpy()
+    lab_ref = oracle.fof_labels(pos_np, spec.L, spec.b)
+    try:
+        for T in (0, 1, 8, 64, 1000):
+            J.set_dense_threshold(T)
+            _, r, H = run_fof(J, pos_np, spec.L, spec.b, spec.min_size)
+            assert np.array_equal(r.label.cpu().numpy(), lab_ref), T
+    finally:
+        J.set_dense_threshold(64)
+
+
 def test_ragged_sizes_and_tiny_boxes(J):
     rng = np.random.default_rng(0)
     for N in (1, 2, 3, 31, 33, 255, 257, 4097):
