@@ -87,11 +87,13 @@ int jfof_set_loop_budget(jfof_ctx *ctx, int64_t iterations);
 int jfof_trace_enable(jfof_ctx *ctx, int on);
 int jfof_trace_read(jfof_ctx *ctx, char *buf, size_t len, size_t *written);
 
-/* Dense-cell threshold: a cell with more than `threshold` particles (and at
-   most 65535) is linked through its sub-cells (see jfof_link); 0 disables
-   that path.  Default 64.  Labels do not depend on it; only speed does.
+/* Cell classes of the link step (see jfof_link): a cell with at most
+   `small_max` particles is "small" (one thread per particle); one with more
+   than `dense_over` (and at most 65535) is "dense" (linked through its
+   sub-cells; 0 disables that path); the rest are "medium" (one warp per
+   cell).  Defaults 8 and 64.  Labels do not depend on them; only speed does.
    Takes effect at the next jfof_bin_cells. */
-int jfof_set_dense_threshold(jfof_ctx *ctx, int32_t threshold);
+int jfof_set_cell_classes(jfof_ctx *ctx, int32_t small_max, int32_t dense_over);
 
 /* ---------------------------------------------------------------------- */
 /* Grid choice (Sec. 2.2, Algorithm 2 "Grid setup").                        */
@@ -117,6 +119,7 @@ typedef struct {
     int32_t brick;        /* cells per brick side (cell table is brick-major) */
     float L, b;           /* box side and linking length */
     uint32_t flags;       /* flags given to jfof_bin_cells */
+    int32_t small_threshold; /* cells with at most this many particles are "small" */
     int32_t dense_threshold; /* cells with more particles take the dense path (0 = off) */
     void *spos;           /* device float4[n]: positions in cell order; .w holds the
                              bits of the int32 original index */

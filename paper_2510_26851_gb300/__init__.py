@@ -25,7 +25,7 @@ JFOF_WRAP = 1
 # Every symbol the header declares (checked by the tests).
 EXPORTED = [
     "jfof_create", "jfof_destroy", "jfof_set_stream", "jfof_sync", "jfof_strerror",
-    "jfof_set_loop_budget", "jfof_set_dense_threshold", "jfof_trace_enable", "jfof_trace_read", "jfof_max_cells_per_axis", "jfof_default_cells_per_axis",
+    "jfof_set_loop_budget", "jfof_set_cell_classes", "jfof_trace_enable", "jfof_trace_read", "jfof_max_cells_per_axis", "jfof_default_cells_per_axis",
     "jfof_fof_bytes", "jfof_bin_cells", "jfof_link", "jfof_groups_bytes", "jfof_groups",
     "jfof_halo_props", "jfof_halo_props_backward", "jfof_fof_all_bytes", "jfof_fof",
 ]
@@ -41,7 +41,8 @@ class Cells(ctypes.Structure):
     """Mirror of ``jfof_cells`` (views into the caller's workspace)."""
     _fields_ = [("n", ctypes.c_int64), ("n_axis", ctypes.c_int32), ("brick", ctypes.c_int32),
                 ("L", ctypes.c_float), ("b", ctypes.c_float), ("flags", ctypes.c_uint32),
-                ("dense_threshold", ctypes.c_int32), ("spos", ctypes.c_void_p),
+                ("small_threshold", ctypes.c_int32), ("dense_threshold", ctypes.c_int32),
+                ("spos", ctypes.c_void_p),
                 ("cell_start", ctypes.c_void_p), ("n_cells_table", ctypes.c_int64),
                 ("workspace", ctypes.c_void_p)]
 
@@ -61,7 +62,7 @@ def _declare(lib):
         "jfof_set_stream": [vp, vp],
         "jfof_sync": [vp],
         "jfof_set_loop_budget": [vp, i64],
-        "jfof_set_dense_threshold": [vp, i32],
+        "jfof_set_cell_classes": [vp, i32, i32],
         "jfof_trace_enable": [vp, c.c_int],
         "jfof_trace_read": [vp, c.c_char_p, sz, P(sz)],
         "jfof_max_cells_per_axis": [f32, f32, P(i32)],
@@ -137,10 +138,11 @@ def set_loop_budget(iterations: int, device=None):
     _check(library().jfof_set_loop_budget(context(device), int(iterations)), "jfof_set_loop_budget")
 
 
-def set_dense_threshold(threshold: int, device=None):
-    """Cells with more particles than this take the dense (sub-cell) path."""
-    _check(library().jfof_set_dense_threshold(context(device), int(threshold)),
-           "jfof_set_dense_threshold")
+def set_cell_classes(small_max: int = 8, dense_over: int = 64, device=None):
+    """Link-step cell classes: <= small_max particles "small", > dense_over
+    "dense" (sub-cell path; 0 disables it), the rest "medium"."""
+    _check(library().jfof_set_cell_classes(context(device), int(small_max), int(dense_over)),
+           "jfof_set_cell_classes")
 
 
 def trace_enable(on: bool = True, device=None):

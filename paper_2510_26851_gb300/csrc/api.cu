@@ -74,8 +74,9 @@ size_t fof_layout(int64_t N, int n, FofBuffers *fb, void *base) {
     f.dense_id = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * size_t(cell_table_entries(n))));
     int64_t D_cap = dense_cap(N);
     f.dense_cells = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * size_t(D_cap)));
-    f.ndense = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t)));
+    f.counters = reinterpret_cast<uint32_t *>(take(2 * sizeof(uint32_t)));
     f.sub_start = reinterpret_cast<uint16_t *>(take(sizeof(uint16_t) * size_t(D_cap) * (kSubMax + 1)));
+    f.medium_cells = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * size_t(medium_cap(N))));
     if (fb) *fb = f;
     return off;
 }
@@ -107,6 +108,7 @@ int jfof_create(jfof_ctx **ctx, int device, void *stream) {
     c->stream = reinterpret_cast<cudaStream_t>(stream);
     c->loop_budget = kDefaultLoopBudget;
     c->dense_threshold = kDefaultDenseThreshold;
+    c->small_threshold = kDefaultSmallThreshold;
     if (cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess) {
         delete c;
         return JFOF_ECUDA;
@@ -193,7 +195,7 @@ int jfof_bin_cells(jfof_ctx *ctx, const float *pos, int64_t N, float L, float b,
     if (ws_bytes < need) return JFOF_ENOMEM;
     cudaSetDevice(ctx->device);
     CtxScope scope(ctx);
-    LinkParams lp = make_link_params(N, L, b, n, ctx->dense_threshold);
+    LinkParams lp = make_link_params(N, L, b, n, ctx->small_threshold, ctx->dense_threshold);
     launch_bin_cells(pos, N, L, n, (flags & JFOF_WRAP) != 0, lp, fb, ctx->dev(), ctx->stream);
     jfof_cells c;
     c.n = N;
@@ -202,6 +204,7 @@ int jfof_bin_cells(jfof_ctx *ctx, const float *pos, int64_t N, float L, float b,
     c.L = L;
     c.b = b;
     c.flags = flags;
+    c.small_threshold = lp.S;
     c.dense_threshold = lp.T;
     c.spos = fb.spos;
     c.cell_start = fb.cell_start;
@@ -219,17 +222,19 @@ int jfof_link(jfof_ctx *ctx, const jfof_cells *cells, int32_t *label) {
     FofBuffers fb;
     fof_layout(cells->n, cells->n_axis, &fb, cells->workspace);
     if (fb.spos != cells->spos || fb.cell_start != cells->cell_start) return JFOF_EINVAL;
-    LinkParams lp = make_link_params(cells->n, cells->L, cells->b, cells->n_axis, cells->dense_threshold);
-    if (lp.T != cells->dense_threshold) return JFOF_EINVAL;
+    LinkParams lp = make_link_params(cells->n, cells->L, cells->b, cells->n_axis, cells->small_threshold,
+                                     cells->dense_threshold);
+    if (lp.T != cells->dense_threshold || lp.S != cells->small_threshold) return JFOF_EINVAL;
     cudaSetDevice(ctx->device);
     CtxScope scope(ctx);
     launch_link(*cells, fb, lp, label, ctx->dev(), ctx->stream);
     return launch_status();
 }
 
-int jfof_set_dense_threshold(jfof_ctx *ctx, int32_t threshold) {
-    if (!ctx || threshold < 0) return JFOF_EINVAL;
-    ctx->dense_threshold = threshold;
+int jfof_set_cell_classes(jfof_ctx *ctx, int32_t small_max, int32_t dense_over) {
+    if (!ctx || small_max < 0 || dense_over < 0) return JFOF_EINVAL;
+    ctx->small_threshold = small_max;
+    ctx->dense_threshold = dense_over;
     return JFOF_OK;
 }
 

@@ -248,6 +248,7 @@ struct jfof_ctx {
     int *h_status;       // pinned host mirror
     int64_t loop_budget;
     int dense_threshold;
+    int small_threshold;
     jfof::DevStatus dev() const { return jfof::DevStatus{d_status, loop_budget}; }
 };
 

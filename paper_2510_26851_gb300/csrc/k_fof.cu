@@ -77,22 +77,26 @@ __global__ void __launch_bounds__(256) bin_scatter_kernel(const float *__restric
 
 // Pass 3: one CTA per brick (persistent loop): shared-memory counting sort of
 // the brick's particles by local cell; writes the brick's 4096 cell starts and
-// registers the dense cells (more than T particles).
+// registers every cell with more than S particles in the medium or the dense
+// work list.
 constexpr int kSortThreads = 512;
 
-struct DenseReg {
-    int T;                    // 0: no dense path
+struct ClassReg {
+    int S, T;                 // small: m <= S; dense: T < m <= kDenseMaxM (T = 0: none)
     uint32_t *dense_id;       // [cell table]
     uint32_t *dense_cells;    // [D_cap]
     uint32_t *ndense;         // counter
     int64_t D_cap;
+    uint32_t *medium_cells;   // [M_cap]
+    uint32_t *nmedium;        // counter
+    int64_t M_cap;
 };
 
 __global__ void __launch_bounds__(kSortThreads) brick_sort_kernel(const float4 *__restrict__ tmp,
                                                                   const uint32_t *__restrict__ brick_start,
                                                                   int64_t n_bricks, BinGeom g,
                                                                   float4 *__restrict__ spos,
-                                                                  uint32_t *__restrict__ cell_start, DenseReg dr) {
+                                                                  uint32_t *__restrict__ cell_start, ClassReg cr) {
     __shared__ uint32_t hist[kBrickCells];
     __shared__ uint32_t warps[kSortThreads / 32];
     constexpr int per = kBrickCells / kSortThreads;  // 8
@@ -124,10 +128,20 @@ __global__ void __launch_bounds__(kSortThreads) brick_sort_kernel(const float4 *
             hist[threadIdx.x * per + k] = pre;
             cell_start[gidx] = bs + pre;
             pre += v[k];
-            if (dr.T > 0 && v[k] > uint32_t(dr.T) && v[k] <= kDenseMaxM) {
-                uint32_t id = atomicAdd(dr.ndense, 1u);
-                dr.dense_id[gidx] = id;
-                if (int64_t(id) < dr.D_cap) dr.dense_cells[id] = uint32_t(gidx);
+            if (v[k] > uint32_t(cr.S)) {
+                bool dense = false;
+                if (cr.T > 0 && v[k] > uint32_t(cr.T) && v[k] <= kDenseMaxM) {
+                    uint32_t id = atomicAdd(cr.ndense, 1u);
+                    cr.dense_id[gidx] = id;
+                    if (int64_t(id) < cr.D_cap) {
+                        cr.dense_cells[id] = uint32_t(gidx);
+                        dense = true;
+                    }
+                }
+                if (!dense) {
+                    uint32_t id = atomicAdd(cr.nmedium, 1u);
+                    if (int64_t(id) < cr.M_cap) cr.medium_cells[id] = uint32_t(gidx);
+                }
             }
         }
         __syncthreads();
@@ -150,7 +164,7 @@ void launch_bin_cells(const float *pos, int64_t N, float L, int n, bool wrap, co
     BinGeom g{L, float(double(n) / double(L)), n, bricks_per_axis(n), wrap};
     int64_t n_bricks = int64_t(g.nb) * g.nb * g.nb;
     cudaMemsetAsync(fb.brick_count, 0, sizeof(uint32_t) * size_t(n_bricks), s);
-    cudaMemsetAsync(fb.ndense, 0, sizeof(uint32_t), s);
+    cudaMemsetAsync(fb.counters, 0, 2 * sizeof(uint32_t), s);
     {
         JFOF_TRACE("bin_count", s);
         bin_count_kernel<<<grid_for(N, 256), 256, 0, s>>>(pos, N, g, fb.brick_count, st);
@@ -164,11 +178,12 @@ void launch_bin_cells(const float *pos, int64_t N, float L, int n, bool wrap, co
         JFOF_TRACE("bin_scatter", s);
         bin_scatter_kernel<<<grid_for(N, 256), 256, 0, s>>>(pos, N, g, fb.cursor, fb.tmp, st);
     }
-    DenseReg dr{lp.T, fb.dense_id, fb.dense_cells, fb.ndense, lp.D_cap};
+    ClassReg cr{lp.S, lp.T, fb.dense_id, fb.dense_cells, fb.counters, lp.D_cap, fb.medium_cells, fb.counters + 1,
+                medium_cap(N)};
     {
         JFOF_TRACE("brick_sort", s);
         brick_sort_kernel<<<grid_for(n_bricks * kSortThreads, kSortThreads, 4), kSortThreads, 0, s>>>(
-            fb.tmp, fb.brick_start, n_bricks, g, fb.spos, fb.cell_start, dr);
+            fb.tmp, fb.brick_start, n_bricks, g, fb.spos, fb.cell_start, cr);
     }
     set_u32_kernel<<<1, 1, 0, s>>>(fb.cell_start + n_bricks * kBrickCells, uint32_t(N));
 }
@@ -177,7 +192,7 @@ void launch_bin_cells(const float *pos, int64_t N, float L, int n, bool wrap, co
 // Link geometry and helpers.
 struct LinkGeom {
     float L, hL, b2, inv_cell, inv_fine, cell_side, gap2;
-    int n, nb, k, k3, T;
+    int n, nb, k, k3, S, T;
     int64_t D_cap;
 };
 
@@ -191,7 +206,9 @@ __constant__ int8_t c_nb26[26][3] = {
     {0, 0, -1},  {-1, 0, -1}, {1, -1, -1}, {0, -1, -1}, {-1, -1, -1}};
 
 // 62 forward sub-cell offsets of the 5x5x5 stencil (first non-zero of
-// (dz, dy, dx) positive); filled on the host at first use.
+// (dz, dy, dx) positive), the 13 with all components in {-1,0,1} first;
+// filled on the host at first use.
+constexpr int kSubNear = 13;
 __constant__ int8_t c_sub62[62][3];
 
 __device__ __forceinline__ void decode_cell(uint32_t gidx, int nb, int &cx, int &cy, int &cz) {
@@ -212,12 +229,34 @@ __device__ __forceinline__ int sub_coord(float x, float inv_fine, int c, int k) 
     return f;
 }
 
-__device__ __forceinline__ bool is_dense(uint32_t m, uint64_t gidx, const LinkGeom &g, const uint32_t *dense_id) {
-    return g.T > 0 && m > uint32_t(g.T) && m <= kDenseMaxM && int64_t(dense_id[gidx]) < g.D_cap;
+// Cell classes: 0 empty, 1 small, 2 medium, 3 dense.
+__device__ __forceinline__ int cell_class(uint32_t m, uint64_t gidx, const LinkGeom &g, const uint32_t *dense_id) {
+    if (m == 0) return 0;
+    if (m <= uint32_t(g.S)) return 1;
+    if (g.T > 0 && m > uint32_t(g.T) && m <= kDenseMaxM && int64_t(dense_id[gidx]) < g.D_cap) return 3;
+    return 2;
 }
 
 __device__ __forceinline__ bool linked(float4 p, float4 q, const LinkGeom &g) {
     return pair_d2(p, q, g.L, g.hL) <= g.b2;
+}
+
+// Squared distance (conservative, float) from a particle to the face/edge/
+// corner a neighbour at offset o shares with its own cell c.
+__device__ __forceinline__ float gap_to_neighbour(float4 p, int cx, int cy, int cz, int ox, int oy, int oz,
+                                                  float side) {
+    float gx = ox > 0 ? float(cx + 1) * side - p.x : (ox < 0 ? p.x - float(cx) * side : 0.f);
+    float gy = oy > 0 ? float(cy + 1) * side - p.y : (oy < 0 ? p.y - float(cy) * side : 0.f);
+    float gz = oz > 0 ? float(cz + 1) * side - p.z : (oz < 0 ? p.z - float(cz) * side : 0.f);
+    gx = fmaxf(gx, 0.f);
+    gy = fmaxf(gy, 0.f);
+    gz = fmaxf(gz, 0.f);
+    return gx * gx + gy * gy + gz * gz;
+}
+
+__device__ __forceinline__ float4 shfl4(float4 v, int src) {
+    return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
+                       __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
 }
 
 __global__ void iota_kernel(int *__restrict__ p, int64_t N) {
@@ -226,13 +265,37 @@ __global__ void iota_kernel(int *__restrict__ p, int64_t N) {
 }
 
 // ---------------------------------------------------------------------------
-// Dense cells: one warp per dense cell.  Counting sort of the cell's particles
-// by sub-cell (staged through tmp), the sub-cell table, then a shared-memory
-// union-find over the cell's sub-cells (a sub-cell is one node: its members
-// are friends), and finally parent[slot] = first slot of the slot's local
-// component.
-constexpr int kDenseWarps = 8;
+// Small cells: one thread per particle.  Pairs with later particles of its
+// cell and with every particle of a small forward neighbour cell that lies
+// within reach (the particle's gap to that cell <= 1.02 b).  All loops are
+// bounded by S.
+__global__ void __launch_bounds__(256) small_kernel(const float4 *__restrict__ spos,
+                                                    const uint32_t *__restrict__ cell_start, int64_t N, LinkGeom g,
+                                                    int *parent, DevStatus st) {
+    for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < N; s += int64_t(gridDim.x) * blockDim.x) {
+        float4 p = spos[s];
+        int cx = cell_coord(p.x, g.inv_cell, g.n), cy = cell_coord(p.y, g.inv_cell, g.n),
+            cz = cell_coord(p.z, g.inv_cell, g.n);
+        uint64_t own = cell_table_index(cx, cy, cz, g.nb);
+        uint32_t a1 = cell_start[own + 1];
+        if (a1 - cell_start[own] > uint32_t(g.S)) continue;
+        for (uint32_t j = uint32_t(s) + 1; j < a1; ++j)
+            if (linked(p, spos[j], g)) uf_unite(parent, int(s), int(j), st);
+        if (g.n < 3) continue;
+#pragma unroll 1
+        for (int o = 0; o < 13; ++o) {
+            int ox = c_nb26[o][0], oy = c_nb26[o][1], oz = c_nb26[o][2];
+            if (gap_to_neighbour(p, cx, cy, cz, ox, oy, oz, g.cell_side) > g.gap2) continue;
+            uint64_t nb = cell_table_index(wrapc(cx + ox, g.n), wrapc(cy + oy, g.n), wrapc(cz + oz, g.n), g.nb);
+            uint32_t b0 = cell_start[nb], b1 = cell_start[nb + 1];
+            if (b1 - b0 > uint32_t(g.S)) continue;  // medium/dense neighbours handle this pair
+            for (uint32_t j = b0; j < b1; ++j)
+                if (linked(p, spos[j], g)) uf_unite(parent, int(s), int(j), st);
+        }
+    }
+}
 
+// ---------------------------------------------------------------------------
 // Path halving in shared memory (each write stores an ancestor of a non-root,
 // so concurrent finds and the CAS hook stay correct, as in uf_find).
 __device__ __forceinline__ int lfind(volatile int *lp, int x) {
@@ -259,6 +322,181 @@ __device__ __forceinline__ void lunite(int *lp, int a, int b) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Medium cells, local part: one warp per cell.  The cell's particles are
+// staged in shared memory and all their pairs tested in 32-wide tiles
+// (lane = one particle, the other broadcast), joined by a shared-memory
+// union-find over local indices; then parent[slot] = first slot of the
+// slot's local component.  A cell larger than the staging area (possible only
+// when it cannot take the dense path) links its own pairs through the global
+// forest instead.  Runs before any kernel that unites across cells, since it
+// writes parent with plain stores.
+constexpr int kMedWarps = 4;
+constexpr int kMedCap = 256;
+
+__global__ void __launch_bounds__(32 * kMedWarps) medium_local_kernel(const float4 *__restrict__ spos,
+                                                                      const uint32_t *__restrict__ cell_start,
+                                                                      const uint32_t *__restrict__ medium_cells,
+                                                                      const uint32_t *__restrict__ nmedium,
+                                                                      int64_t M_cap, LinkGeom g, int *parent,
+                                                                      DevStatus st) {
+    __shared__ float4 sh_p[kMedWarps][kMedCap];
+    __shared__ int sh_l[kMedWarps][kMedCap];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float4 *sp = sh_p[w];
+    int *lp = sh_l[w];
+    int64_t M = *nmedium;
+    if (M > M_cap) M = M_cap;
+    for (int64_t t = int64_t(blockIdx.x) * kMedWarps + w; t < M; t += int64_t(gridDim.x) * kMedWarps) {
+        uint32_t ga = medium_cells[t];
+        uint32_t a0 = cell_start[ga];
+        int mA = int(cell_start[ga + 1] - a0);
+        if (mA > kMedCap) {
+            for (int i = 0; i < mA - 1; ++i) {
+                float4 pi = spos[a0 + i];
+                for (int j = i + 1 + lane; j < mA; j += 32)
+                    if (linked(pi, spos[a0 + j], g)) uf_unite(parent, int(a0 + i), int(a0 + j), st);
+            }
+            continue;
+        }
+        for (int q = lane; q < mA; q += 32) {
+            sp[q] = spos[a0 + q];
+            lp[q] = q;
+        }
+        __syncwarp();
+        for (int cb = 0; cb * 32 < mA; ++cb) {
+            int j = cb * 32 + lane;
+            bool has = j < mA;
+            float4 pj = has ? sp[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+            int iend = min(mA, cb * 32 + 32) - 1;
+            for (int i = 0; i < iend; ++i) {
+                float4 pi = sp[i];
+                if (has && i < j && linked(pi, pj, g)) lunite(lp, i, j);
+            }
+        }
+        __syncwarp();
+        for (int q = lane; q < mA; q += 32) parent[a0 + q] = int(a0) + lfind(lp, q);
+        __syncwarp();
+    }
+}
+
+// Medium cells, cross part: one warp per cell.  For each small neighbour
+// (any direction) and each medium forward neighbour, the particles of both
+// cells that lie within reach of the shared face/edge/corner are selected by
+// ballot and their cross pairs spread over lanes.
+__global__ void __launch_bounds__(256) medium_kernel(const float4 *__restrict__ spos,
+                                                     const uint32_t *__restrict__ cell_start,
+                                                     const uint32_t *__restrict__ medium_cells,
+                                                     const uint32_t *__restrict__ nmedium,
+                                                     const uint32_t *__restrict__ dense_id, int64_t M_cap,
+                                                     LinkGeom g, int *parent, DevStatus st) {
+    const int lane = threadIdx.x & 31;
+    int64_t M = *nmedium;
+    if (M > M_cap) M = M_cap;
+    int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t t = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; t < M; t += nw) {
+        uint32_t ga = medium_cells[t];
+        int cx, cy, cz;
+        decode_cell(ga, g.nb, cx, cy, cz);
+        uint32_t a0 = cell_start[ga];
+        int mA = int(cell_start[ga + 1] - a0);
+        if (g.n < 3) continue;
+        uint32_t nb0 = 0, nb1 = 0;
+        int ncls = 0;
+        if (lane < 26) {
+            uint64_t gb = cell_table_index(wrapc(cx + c_nb26[lane][0], g.n), wrapc(cy + c_nb26[lane][1], g.n),
+                                           wrapc(cz + c_nb26[lane][2], g.n), g.nb);
+            nb0 = cell_start[gb];
+            nb1 = cell_start[gb + 1];
+            ncls = cell_class(nb1 - nb0, gb, g, dense_id);
+        }
+        for (int o = 0; o < 26; ++o) {
+            int cls = __shfl_sync(0xffffffffu, ncls, o);
+            if (cls == 0 || cls == 3 || (cls == 2 && o >= 13)) continue;
+            uint32_t b0 = __shfl_sync(0xffffffffu, nb0, o), b1 = __shfl_sync(0xffffffffu, nb1, o);
+            int ox = c_nb26[o][0], oy = c_nb26[o][1], oz = c_nb26[o][2];
+            int bx = wrapc(cx + ox, g.n), by = wrapc(cy + oy, g.n), bz = wrapc(cz + oz, g.n);
+            int mB = int(b1 - b0);
+            for (int ca = 0; ca < mA; ca += 32) {
+                int i = ca + lane;
+                float4 pa = make_float4(0.f, 0.f, 0.f, 0.f);
+                bool ina = i < mA;
+                if (ina) {
+                    pa = spos[a0 + i];
+                    ina = gap_to_neighbour(pa, cx, cy, cz, ox, oy, oz, g.cell_side) <= g.gap2;
+                }
+                unsigned ma = __ballot_sync(0xffffffffu, ina);
+                if (!ma) continue;
+                for (int cb = 0; cb < mB; cb += 32) {
+                    int j = cb + lane;
+                    float4 qb = make_float4(0.f, 0.f, 0.f, 0.f);
+                    bool inb = j < mB;
+                    if (inb) {
+                        qb = spos[b0 + j];
+                        inb = gap_to_neighbour(qb, bx, by, bz, -ox, -oy, -oz, g.cell_side) <= g.gap2;
+                    }
+                    if (!__ballot_sync(0xffffffffu, inb)) continue;
+                    unsigned bits = ma;
+                    while (bits) {
+                        int src = __ffs(bits) - 1;
+                        bits &= bits - 1;
+                        float4 x = shfl4(pa, src);
+                        if (inb && linked(x, qb, g)) uf_unite(parent, int(a0 + ca + src), int(b0 + j), st);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Dense cells, part 1: one warp per dense cell.  Counting sort of the cell's
+// particles by sub-cell (staged through tmp), the sub-cell table, then a
+// shared-memory union-find over the cell's sub-cells (a sub-cell is one node:
+// its members are friends), processing the 13 adjacent forward offsets for
+// every non-empty sub-cell first and the other 49 after, with the
+// (sub-cell, offset) work spread over lanes; finally
+// parent[slot] = first slot of the slot's local component.
+constexpr int kDenseWarps = 4;
+
+__device__ __forceinline__ int sub_key(float4 q, const LinkGeom &g, int cx, int cy, int cz) {
+    return sub_coord(q.x, g.inv_fine, cx, g.k) +
+           g.k * (sub_coord(q.y, g.inv_fine, cy, g.k) + g.k * sub_coord(q.z, g.inv_fine, cz, g.k));
+}
+
+// One round of the dense-cell local union-find: every (non-empty sub-cell,
+// forward offset O0..O0+R-1) task, spread over the lanes; a task is skipped
+// when the two sub-cells are already in one component, else the pair of
+// sub-cells is tested until its first link.
+template <int O0, int R>
+__device__ __forceinline__ void dense_round(const uint16_t *ne, int nF, int k, const uint16_t *ss, int *lp,
+                                            const float4 *__restrict__ cp, const LinkGeom &g, int lane) {
+    const int total = nF * R;
+    for (int p = lane; p < total; p += 32) {
+        int F = ne[p / R];
+        int o = O0 + p % R;
+        int fz = F / (k * k), rem = F - fz * k * k, fy = rem / k, fx = rem - fy * k;
+        int gx = fx + c_sub62[o][0], gy = fy + c_sub62[o][1], gz = fz + c_sub62[o][2];
+        if (unsigned(gx) >= unsigned(k) || unsigned(gy) >= unsigned(k) || unsigned(gz) >= unsigned(k)) continue;
+        int G = gx + k * (gy + k * gz);
+        int g0 = ss[G], g1 = ss[G + 1];
+        if (g0 == g1) continue;
+        if (lfind(lp, F) == lfind(lp, G)) continue;
+        int f0 = ss[F], f1 = ss[F + 1];
+        bool done = false;
+        for (int a = f0; a < f1 && !done; ++a) {
+            float4 pa = cp[a];
+            for (int c = g0; c < g1; ++c) {
+                if (linked(pa, cp[c], g)) {
+                    lunite(lp, F, G);
+                    done = true;
+                    break;
+                }
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(32 * kDenseWarps) dense_cells_kernel(float4 *__restrict__ spos,
                                                                        float4 *__restrict__ stage,
                                                                        const uint32_t *__restrict__ cell_start,
@@ -268,9 +506,11 @@ __global__ void __launch_bounds__(32 * kDenseWarps) dense_cells_kernel(float4 *_
                                                                        int *__restrict__ parent, LinkGeom g) {
     __shared__ int sh_cnt[kDenseWarps][kSubMax + 1];
     __shared__ uint16_t sh_ss[kDenseWarps][kSubMax + 2];
+    __shared__ uint16_t sh_ne[kDenseWarps][kSubMax + 1];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int *cnt = sh_cnt[w];
     uint16_t *ss = sh_ss[w];
+    uint16_t *ne = sh_ne[w];
     int64_t D = *ndense;
     if (D > g.D_cap) D = g.D_cap;
     const int k = g.k, k3 = g.k3;
@@ -285,28 +525,35 @@ __global__ void __launch_bounds__(32 * kDenseWarps) dense_cells_kernel(float4 *_
         for (int t = lane; t < m; t += 32) {
             float4 q = spos[start + t];
             stage[start + t] = q;
-            int key = sub_coord(q.x, g.inv_fine, cx, k) + k * (sub_coord(q.y, g.inv_fine, cy, k) +
-                                                               k * sub_coord(q.z, g.inv_fine, cz, k));
-            atomicAdd(&cnt[key], 1);
+            atomicAdd(&cnt[sub_key(q, g, cx, cy, cz)], 1);
         }
         __syncwarp();
-        // exclusive scan of the k3 counts: lane owns a contiguous chunk
+        // exclusive scan of the k3 counts (lane owns a contiguous chunk) and
+        // the compact list of non-empty sub-cells
         const int chunk = (k3 + 31) / 32;
         int lo = lane * chunk, hi = min(lo + chunk, k3);
-        int sum = 0;
-        for (int key = lo; key < hi; ++key) sum += cnt[key];
-        int x = sum;
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
+        int sum = 0, nz = 0;
+        for (int key = lo; key < hi; ++key) {
+            sum += cnt[key];
+            nz += cnt[key] > 0;
         }
-        int pre = x - sum;
+        int xs = sum, xn = nz;
+        for (int o = 1; o < 32; o <<= 1) {
+            int ys = __shfl_up_sync(0xffffffffu, xs, o), yn = __shfl_up_sync(0xffffffffu, xn, o);
+            if (lane >= o) {
+                xs += ys;
+                xn += yn;
+            }
+        }
+        int pre = xs - sum, pn = xn - nz;
+        int nF = __shfl_sync(0xffffffffu, xn, 31);
         uint16_t *tab = sub_start + d * (kSubMax + 1);
         for (int key = lo; key < hi; ++key) {
             int c = cnt[key];
             ss[key] = uint16_t(pre);
             tab[key] = uint16_t(pre);
             cnt[key] = pre;
+            if (c > 0) ne[pn++] = uint16_t(key);
             pre += c;
         }
         if (lane == 0) {
@@ -316,202 +563,153 @@ __global__ void __launch_bounds__(32 * kDenseWarps) dense_cells_kernel(float4 *_
         __syncwarp();
         for (int t = lane; t < m; t += 32) {
             float4 q = stage[start + t];
-            int key = sub_coord(q.x, g.inv_fine, cx, k) + k * (sub_coord(q.y, g.inv_fine, cy, k) +
-                                                               k * sub_coord(q.z, g.inv_fine, cz, k));
-            int r = atomicAdd(&cnt[key], 1);
+            int r = atomicAdd(&cnt[sub_key(q, g, cx, cy, cz)], 1);
             spos[start + r] = q;
         }
         __syncwarp();
-        // local union-find over sub-cells (cnt reused as the forest)
         for (int key = lane; key < k3; key += 32) cnt[key] = key;
         __syncwarp();
-        for (int F = lane; F < k3; F += 32) {
-            int f0 = ss[F], f1 = ss[F + 1];
-            if (f0 == f1) continue;
-            int fx = F % k, fy = (F / k) % k, fz = F / (k * k);
-            for (int o = 0; o < 62; ++o) {
-                int gx = fx + c_sub62[o][0], gy = fy + c_sub62[o][1], gz = fz + c_sub62[o][2];
-                if (gx < 0 || gx >= k || gy < 0 || gy >= k || gz < 0 || gz >= k) continue;
-                int G = gx + k * (gy + k * gz);
-                int g0 = ss[G], g1 = ss[G + 1];
-                if (g0 == g1) continue;
-                if (lfind(cnt, F) == lfind(cnt, G)) continue;
-                bool done = false;
-                for (int a = f0; a < f1 && !done; ++a) {
-                    float4 p = spos[start + a];
-                    for (int c = g0; c < g1; ++c) {
-                        if (linked(p, spos[start + c], g)) {
-                            lunite(cnt, F, G);
-                            done = true;
-                            break;
-                        }
-                    }
-                }
-            }
-        }
+        dense_round<0, kSubNear>(ne, nF, k, ss, cnt, spos + start, g, lane);
+        __syncwarp();
+        // the second round (offsets with a component of +-2) can only join
+        // sub-cells still in different components: skip it when one is left
+        bool split = false;
+        int r0 = lfind(cnt, ne[0]);
+        for (int i = lane; i < nF; i += 32) split |= lfind(cnt, ne[i]) != r0;
+        if (__any_sync(0xffffffffu, split)) dense_round<kSubNear, 62 - kSubNear>(ne, nF, k, ss, cnt, spos + start, g, lane);
         __syncwarp();
         for (int t = lane; t < m; t += 32) {
             float4 q = spos[start + t];
-            int key = sub_coord(q.x, g.inv_fine, cx, k) + k * (sub_coord(q.y, g.inv_fine, cy, k) +
-                                                               k * sub_coord(q.z, g.inv_fine, cz, k));
-            parent[start + t] = int(start) + ss[lfind(cnt, key)];
+            parent[start + t] = int(start) + ss[lfind(cnt, sub_key(q, g, cx, cy, cz))];
         }
         __syncwarp();
     }
 }
 
 // ---------------------------------------------------------------------------
-// Sparse probes: one thread per particle of a sparse cell.  Pairs with later
-// particles of its own cell; with every particle of a sparse forward
-// neighbour cell (skipped when the particle is farther than b from that
-// cell); and with the sub-cells of any dense neighbour cell within reach.
-__global__ void __launch_bounds__(256) probe_kernel(const float4 *__restrict__ spos,
-                                                    const uint32_t *__restrict__ cell_start,
-                                                    const uint32_t *__restrict__ dense_id,
-                                                    const uint16_t *__restrict__ sub_start, int64_t N, LinkGeom g,
-                                                    int *parent, DevStatus st) {
-    for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < N; s += int64_t(gridDim.x) * blockDim.x) {
-        float4 p = spos[s];
-        int cx = cell_coord(p.x, g.inv_cell, g.n), cy = cell_coord(p.y, g.inv_cell, g.n),
-            cz = cell_coord(p.z, g.inv_cell, g.n);
-        uint64_t own = cell_table_index(cx, cy, cz, g.nb);
-        uint32_t a0 = cell_start[own], a1 = cell_start[own + 1];
-        if (is_dense(a1 - a0, own, g, dense_id)) continue;
-        for (uint32_t j = uint32_t(s) + 1; j < a1; ++j)
-            if (linked(p, spos[j], g)) uf_unite(parent, int(s), int(j), st);
-        if (g.n < 3) continue;
-        // gaps to the lower / upper faces of the own cell (for pruning)
-        float lo_gap[3], hi_gap[3];
-        {
-            float pc[3] = {p.x, p.y, p.z};
-            int cc[3] = {cx, cy, cz};
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                lo_gap[a] = pc[a] - float(cc[a]) * g.cell_side;
-                hi_gap[a] = float(cc[a] + 1) * g.cell_side - pc[a];
-            }
-        }
-        int lf[3] = {-1, -1, -1};
-#pragma unroll 1
-        for (int o = 0; o < 26; ++o) {
-            int ox = c_nb26[o][0], oy = c_nb26[o][1], oz = c_nb26[o][2];
-            float gx = ox > 0 ? hi_gap[0] : (ox < 0 ? lo_gap[0] : 0.f);
-            float gy = oy > 0 ? hi_gap[1] : (oy < 0 ? lo_gap[1] : 0.f);
-            float gz = oz > 0 ? hi_gap[2] : (oz < 0 ? lo_gap[2] : 0.f);
-            gx = fmaxf(gx, 0.f);
-            gy = fmaxf(gy, 0.f);
-            gz = fmaxf(gz, 0.f);
-            if (gx * gx + gy * gy + gz * gz > g.gap2) continue;
-            int nx = wrapc(cx + ox, g.n), ny = wrapc(cy + oy, g.n), nz = wrapc(cz + oz, g.n);
-            uint64_t nb = cell_table_index(nx, ny, nz, g.nb);
-            uint32_t b0 = cell_start[nb], b1 = cell_start[nb + 1];
-            if (b0 == b1) continue;
-            if (!is_dense(b1 - b0, nb, g, dense_id)) {
-                if (o >= 13) continue;  // the other cell's forward pass covers it
-                for (uint32_t j = b0; j < b1; ++j)
-                    if (linked(p, spos[j], g)) uf_unite(parent, int(s), int(j), st);
-                continue;
-            }
-            if (lf[0] < 0) {
-                lf[0] = sub_coord(p.x, g.inv_fine, cx, g.k);
-                lf[1] = sub_coord(p.y, g.inv_fine, cy, g.k);
-                lf[2] = sub_coord(p.z, g.inv_fine, cz, g.k);
-            }
-            int off[3] = {ox, oy, oz}, lo[3], hi[3];
-            bool empty = false;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                int c = lf[a] - off[a] * g.k;
-                lo[a] = max(c - 2, 0);
-                hi[a] = min(c + 2, g.k - 1);
-                empty |= lo[a] > hi[a];
-            }
-            if (empty) continue;
-            const uint16_t *tab = sub_start + int64_t(dense_id[nb]) * (kSubMax + 1);
-            for (int zz = lo[2]; zz <= hi[2]; ++zz)
-                for (int yy = lo[1]; yy <= hi[1]; ++yy)
-                    for (int xx = lo[0]; xx <= hi[0]; ++xx) {
-                        int G = xx + g.k * (yy + g.k * zz);
-                        uint32_t c0 = tab[G], c1 = tab[G + 1];
-                        if (c0 == c1) continue;
-                        if (uf_find(parent, int(s)) == uf_find(parent, int(b0 + c0))) continue;
-                        for (uint32_t c = c0; c < c1; ++c)
-                            if (linked(p, spos[b0 + c], g)) {
-                                uf_unite(parent, int(s), int(b0 + c), st);
-                                break;
-                            }
-                    }
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Dense-dense neighbour pairs: one warp per (dense cell, forward offset) whose
-// neighbour is also dense.  Sub-cells of A within reach of B against the
-// sub-cells of B within reach of each: skipped when already in one
-// component, else tested until the first link.
-__global__ void __launch_bounds__(256) dense_pairs_kernel(const float4 *__restrict__ spos,
-                                                          const uint32_t *__restrict__ cell_start,
-                                                          const uint32_t *__restrict__ dense_cells,
-                                                          const uint32_t *__restrict__ ndense,
-                                                          const uint32_t *__restrict__ dense_id,
-                                                          const uint16_t *__restrict__ sub_start, LinkGeom g,
-                                                          int *parent, DevStatus st) {
+// Dense cells, part 2: one warp per dense cell, its pairs with neighbours.
+// Small and medium neighbours (any direction): each neighbour particle within
+// reach of the shared face is probed against the cell's sub-cells within 2
+// sub-cells of it (lanes over sub-cells): skipped when already in one
+// component, else tested until the first link.  Dense forward neighbours:
+// every boundary sub-cell of this cell (lanes) against the neighbour's
+// sub-cells within reach, the same way.
+__global__ void __launch_bounds__(256) dense_nbr_kernel(const float4 *__restrict__ spos,
+                                                        const uint32_t *__restrict__ cell_start,
+                                                        const uint32_t *__restrict__ dense_cells,
+                                                        const uint32_t *__restrict__ ndense,
+                                                        const uint32_t *__restrict__ dense_id,
+                                                        const uint16_t *__restrict__ sub_start, LinkGeom g,
+                                                        int *parent, DevStatus st) {
     const int lane = threadIdx.x & 31;
     int64_t D = *ndense;
     if (D > g.D_cap) D = g.D_cap;
     const int k = g.k;
     int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
-    for (int64_t task = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; task < D * 13; task += nw) {
-        int64_t d = task / 13;
-        int o = int(task % 13);
+    for (int64_t d = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; d < D; d += nw) {
+        if (g.n < 3) break;
         uint32_t ga = dense_cells[d];
         int cx, cy, cz;
         decode_cell(ga, g.nb, cx, cy, cz);
-        int off[3] = {c_nb26[o][0], c_nb26[o][1], c_nb26[o][2]};
-        uint64_t gb = cell_table_index(wrapc(cx + off[0], g.n), wrapc(cy + off[1], g.n), wrapc(cz + off[2], g.n), g.nb);
-        uint32_t b0 = cell_start[gb], b1 = cell_start[gb + 1];
-        if (!is_dense(b1 - b0, gb, g, dense_id)) continue;
         uint32_t a0 = cell_start[ga];
         const uint16_t *ta = sub_start + d * (kSubMax + 1);
-        const uint16_t *tb = sub_start + int64_t(dense_id[gb]) * (kSubMax + 1);
-        int flo[3], fn[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            flo[a] = off[a] > 0 ? k - 2 : 0;
-            fn[a] = off[a] != 0 ? 2 : k;
+        uint32_t nb0 = 0, nb1 = 0, nid = 0;
+        int ncls = 0;
+        if (lane < 26) {
+            uint64_t gb = cell_table_index(wrapc(cx + c_nb26[lane][0], g.n), wrapc(cy + c_nb26[lane][1], g.n),
+                                           wrapc(cz + c_nb26[lane][2], g.n), g.nb);
+            nb0 = cell_start[gb];
+            nb1 = cell_start[gb + 1];
+            ncls = cell_class(nb1 - nb0, gb, g, dense_id);
+            if (ncls == 3) nid = dense_id[gb];
         }
-        int nF = fn[0] * fn[1] * fn[2];
-        for (int f = lane; f < nF; f += 32) {
-            int fx = flo[0] + f % fn[0], fy = flo[1] + (f / fn[0]) % fn[1], fz = flo[2] + f / (fn[0] * fn[1]);
-            int F = fx + k * (fy + k * fz);
-            uint32_t f0 = ta[F], f1 = ta[F + 1];
-            if (f0 == f1) continue;
-            int fc[3] = {fx, fy, fz}, lo[3], hi[3];
+        for (int o = 0; o < 26; ++o) {
+            int cls = __shfl_sync(0xffffffffu, ncls, o);
+            if (cls == 0 || (cls == 3 && o >= 13)) continue;
+            uint32_t b0 = __shfl_sync(0xffffffffu, nb0, o), b1 = __shfl_sync(0xffffffffu, nb1, o);
+            int off[3] = {c_nb26[o][0], c_nb26[o][1], c_nb26[o][2]};
+            int bx = wrapc(cx + off[0], g.n), by = wrapc(cy + off[1], g.n), bz = wrapc(cz + off[2], g.n);
+            if (cls != 3) {
+                int mB = int(b1 - b0);
+                for (int cb = 0; cb < mB; cb += 32) {
+                    int j = cb + lane;
+                    float4 qb = make_float4(0.f, 0.f, 0.f, 0.f);
+                    bool inb = j < mB;
+                    if (inb) {
+                        qb = spos[b0 + j];
+                        inb = gap_to_neighbour(qb, bx, by, bz, -off[0], -off[1], -off[2], g.cell_side) <= g.gap2;
+                    }
+                    unsigned bits = __ballot_sync(0xffffffffu, inb);
+                    while (bits) {
+                        int src = __ffs(bits) - 1;
+                        bits &= bits - 1;
+                        float4 q = shfl4(qb, src);
+                        int lq[3] = {sub_coord(q.x, g.inv_fine, bx, k), sub_coord(q.y, g.inv_fine, by, k),
+                                     sub_coord(q.z, g.inv_fine, bz, k)};
+                        int lo[3], n3[3];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                int c = fc[a] - off[a] * k;
-                lo[a] = max(c - 2, 0);
-                hi[a] = min(c + 2, k - 1);
-            }
-            for (int zz = lo[2]; zz <= hi[2]; ++zz)
-                for (int yy = lo[1]; yy <= hi[1]; ++yy)
-                    for (int xx = lo[0]; xx <= hi[0]; ++xx) {
-                        int G = xx + k * (yy + k * zz);
-                        uint32_t c0 = tb[G], c1 = tb[G + 1];
-                        if (c0 == c1) continue;
-                        if (uf_find(parent, int(a0 + f0)) == uf_find(parent, int(b0 + c0))) continue;
-                        bool done = false;
-                        for (uint32_t a = f0; a < f1 && !done; ++a) {
-                            float4 p = spos[a0 + a];
+                        for (int a = 0; a < 3; ++a) {
+                            int c = lq[a] + off[a] * k;  // q's sub-cell in this cell's frame
+                            lo[a] = max(c - 2, 0);
+                            n3[a] = min(c + 2, k - 1) - lo[a] + 1;
+                        }
+                        if (n3[0] <= 0 || n3[1] <= 0 || n3[2] <= 0) continue;
+                        int nbox = n3[0] * n3[1] * n3[2];
+                        int qs = int(b0 + cb + src);
+                        for (int t = lane; t < nbox; t += 32) {
+                            int G = (lo[0] + t % n3[0]) + k * ((lo[1] + (t / n3[0]) % n3[1]) + k * (lo[2] + t / (n3[0] * n3[1])));
+                            uint32_t c0 = ta[G], c1 = ta[G + 1];
+                            if (c0 == c1) continue;
+                            if (uf_find(parent, qs) == uf_find(parent, int(a0 + c0))) continue;
                             for (uint32_t c = c0; c < c1; ++c)
-                                if (linked(p, spos[b0 + c], g)) {
-                                    uf_unite(parent, int(a0 + a), int(b0 + c), st);
-                                    done = true;
+                                if (linked(q, spos[a0 + c], g)) {
+                                    uf_unite(parent, qs, int(a0 + c), st);
                                     break;
                                 }
                         }
                     }
+                }
+                continue;
+            }
+            const uint16_t *tb = sub_start + int64_t(__shfl_sync(0xffffffffu, nid, o)) * (kSubMax + 1);
+            int flo[3], fn[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                flo[a] = off[a] > 0 ? k - 2 : 0;
+                fn[a] = off[a] != 0 ? 2 : k;
+            }
+            int nFb = fn[0] * fn[1] * fn[2];
+            for (int f = lane; f < nFb; f += 32) {
+                int fc[3] = {flo[0] + f % fn[0], flo[1] + (f / fn[0]) % fn[1], flo[2] + f / (fn[0] * fn[1])};
+                int F = fc[0] + k * (fc[1] + k * fc[2]);
+                uint32_t f0 = ta[F], f1 = ta[F + 1];
+                if (f0 == f1) continue;
+                int lo[3], hi[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    int c = fc[a] - off[a] * k;
+                    lo[a] = max(c - 2, 0);
+                    hi[a] = min(c + 2, k - 1);
+                }
+                for (int zz = lo[2]; zz <= hi[2]; ++zz)
+                    for (int yy = lo[1]; yy <= hi[1]; ++yy)
+                        for (int xx = lo[0]; xx <= hi[0]; ++xx) {
+                            int G = xx + k * (yy + k * zz);
+                            uint32_t c0 = tb[G], c1 = tb[G + 1];
+                            if (c0 == c1) continue;
+                            if (uf_find(parent, int(a0 + f0)) == uf_find(parent, int(b0 + c0))) continue;
+                            bool done = false;
+                            for (uint32_t a = f0; a < f1 && !done; ++a) {
+                                float4 p = spos[a0 + a];
+                                for (uint32_t c = c0; c < c1; ++c)
+                                    if (linked(p, spos[b0 + c], g)) {
+                                        uf_unite(parent, int(a0 + a), int(b0 + c), st);
+                                        done = true;
+                                        break;
+                                    }
+                            }
+                        }
+            }
         }
     }
 }
@@ -545,21 +743,23 @@ static void ensure_sub_offsets() {
     if (g_sub62_ready) return;
     int8_t t[62][3];
     int c = 0;
-    for (int dz = -2; dz <= 2; ++dz)
-        for (int dy = -2; dy <= 2; ++dy)
-            for (int dx = -2; dx <= 2; ++dx) {
-                bool fwd = dz > 0 || (dz == 0 && (dy > 0 || (dy == 0 && dx > 0)));
-                if (!fwd) continue;
-                t[c][0] = int8_t(dx);
-                t[c][1] = int8_t(dy);
-                t[c][2] = int8_t(dz);
-                ++c;
-            }
+    for (int pass = 0; pass < 2; ++pass)
+        for (int dz = -2; dz <= 2; ++dz)
+            for (int dy = -2; dy <= 2; ++dy)
+                for (int dx = -2; dx <= 2; ++dx) {
+                    bool fwd = dz > 0 || (dz == 0 && (dy > 0 || (dy == 0 && dx > 0)));
+                    bool near = dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1;
+                    if (!fwd || near != (pass == 0)) continue;
+                    t[c][0] = int8_t(dx);
+                    t[c][1] = int8_t(dy);
+                    t[c][2] = int8_t(dz);
+                    ++c;
+                }
     cudaMemcpyToSymbol(c_sub62, t, sizeof(t));
     g_sub62_ready = true;
 }
 
-LinkParams make_link_params(int64_t N, float L, float b, int n, int T) {
+LinkParams make_link_params(int64_t N, float L, float b, int n, int S, int T) {
     LinkParams lp{};
     double s = double(L) / n;
     int k = int(std::ceil(s * std::sqrt(3.0) * 1.02 / double(b)));
@@ -568,10 +768,11 @@ LinkParams make_link_params(int64_t N, float L, float b, int n, int T) {
     double eps = 4.0 * double(L) * std::ldexp(1.0, -24);
     bool ok = T > 0 && n >= 5 && k <= kSubSide && std::sqrt(3.0) * (sf + 2 * eps) <= double(b) * (1 - 1e-4) &&
               (double(b) + 2 * eps) / sf < 2.0;
-    lp.T = ok ? T : 0;
+    lp.S = S < 0 ? 0 : S;
+    lp.T = ok ? (T > lp.S ? T : lp.S + 1) : 0;
     lp.k = k;
     lp.inv_fine = float(double(n) * k / double(L));
-    lp.D_cap = ok ? N / 256 + 1024 : 0;
+    lp.D_cap = ok ? dense_cap(N) : 0;
     return lp;
 }
 
@@ -583,26 +784,37 @@ void launch_link(const jfof_cells &c, const FofBuffers &fb, const LinkParams &lp
     double gap = 1.02 * double(c.b);
     LinkGeom g{c.L, 0.5f * c.L, b2, float(double(c.n_axis) / double(c.L)), lp.inv_fine,
                float(double(c.L) / c.n_axis), float(gap * gap), c.n_axis, bricks_per_axis(c.n_axis), lp.k,
-               lp.k * lp.k * lp.k, lp.T, lp.D_cap};
+               lp.k * lp.k * lp.k, lp.S, lp.T, lp.D_cap};
     const float4 *spos = reinterpret_cast<const float4 *>(c.spos);
     {
         JFOF_TRACE("link_init", s);
         iota_kernel<<<grid_for(N, 256), 256, 0, s>>>(fb.parent, N);
     }
+    // local passes first: they write parent with plain stores, each for its own cell
     if (lp.T > 0) {
         JFOF_TRACE("dense_cells", s);
-        dense_cells_kernel<<<grid_for(lp.D_cap * 32, 32 * kDenseWarps, 4), 32 * kDenseWarps, 0, s>>>(
-            fb.spos, fb.tmp, c.cell_start, fb.dense_cells, fb.ndense, fb.sub_start, fb.parent, g);
+        dense_cells_kernel<<<grid_for(lp.D_cap * 32, 32 * kDenseWarps, 8), 32 * kDenseWarps, 0, s>>>(
+            fb.spos, fb.tmp, c.cell_start, fb.dense_cells, fb.counters, fb.sub_start, fb.parent, g);
     }
     {
-        JFOF_TRACE("link", s);
-        probe_kernel<<<grid_for(N, 256), 256, 0, s>>>(spos, c.cell_start, fb.dense_id, fb.sub_start, N, g,
-                                                       fb.parent, st);
+        JFOF_TRACE("link_medium_local", s);
+        medium_local_kernel<<<grid_for(medium_cap(N) * 32, 32 * kMedWarps, 8), 32 * kMedWarps, 0, s>>>(
+            spos, c.cell_start, fb.medium_cells, fb.counters + 1, medium_cap(N), g, fb.parent, st);
+    }
+    // then everything that unites across cells (atomic hooks only)
+    if (lp.S > 0) {
+        JFOF_TRACE("link_small", s);
+        small_kernel<<<grid_for(N, 256), 256, 0, s>>>(spos, c.cell_start, N, g, fb.parent, st);
+    }
+    {
+        JFOF_TRACE("link_medium", s);
+        medium_kernel<<<grid_for(medium_cap(N) * 32, 256, 8), 256, 0, s>>>(
+            spos, c.cell_start, fb.medium_cells, fb.counters + 1, fb.dense_id, medium_cap(N), g, fb.parent, st);
     }
     if (lp.T > 0) {
-        JFOF_TRACE("dense_pairs", s);
-        dense_pairs_kernel<<<grid_for(lp.D_cap * 13 * 32, 256, 8), 256, 0, s>>>(
-            spos, c.cell_start, fb.dense_cells, fb.ndense, fb.dense_id, fb.sub_start, g, fb.parent, st);
+        JFOF_TRACE("link_dense_nbr", s);
+        dense_nbr_kernel<<<grid_for(lp.D_cap * 32, 256, 8), 256, 0, s>>>(
+            spos, c.cell_start, fb.dense_cells, fb.counters, fb.dense_id, fb.sub_start, g, fb.parent, st);
     }
     int *rootmin = reinterpret_cast<int *>(fb.tmp);
     cudaMemsetAsync(rootmin, 0x7f, sizeof(int) * size_t(N), s);

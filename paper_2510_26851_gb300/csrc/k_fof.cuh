@@ -12,6 +12,7 @@ constexpr int kSubSide = 9;
 constexpr int kSubMax = kSubSide * kSubSide * kSubSide;  // 729
 constexpr uint32_t kDenseMaxM = 65535;
 constexpr int kDefaultDenseThreshold = 64;
+constexpr int kDefaultSmallThreshold = 8;
 
 // One IEEE binary32 multiply on the host (b*b for the link threshold).
 inline float host_mul(float a, float b) {
@@ -20,6 +21,7 @@ inline float host_mul(float a, float b) {
 }
 
 inline int64_t dense_cap(int64_t N) { return N / 256 + 1024; }
+inline int64_t medium_cap(int64_t N) { return N + 16; }
 
 // Views into the bin/link workspace.
 struct FofBuffers {
@@ -33,12 +35,14 @@ struct FofBuffers {
     int *parent;           // [N]
     uint32_t *dense_id;    // [cell table]
     uint32_t *dense_cells; // [D_cap]
-    uint32_t *ndense;      // [1]
+    uint32_t *counters;    // [2]: dense cells, medium cells
     uint16_t *sub_start;   // [D_cap][kSubMax + 1]
+    uint32_t *medium_cells;// [medium_cap]
 };
 
 // Dense-path parameters derived on the host from (N, L, b, n, T).
 struct LinkParams {
+    int S;          // small cells: at most S particles
     int T;          // dense threshold actually used (0 = dense path off)
     int k;          // sub-cells per cell side
     float inv_fine; // f32(n k / L)
@@ -46,7 +50,7 @@ struct LinkParams {
 };
 
 size_t fof_layout(int64_t N, int n, FofBuffers *fb, void *base);
-LinkParams make_link_params(int64_t N, float L, float b, int n, int T);
+LinkParams make_link_params(int64_t N, float L, float b, int n, int S, int T);
 void launch_bin_cells(const float *pos, int64_t N, float L, int n, bool wrap, const LinkParams &lp,
                       const FofBuffers &fb, const DevStatus &st, cudaStream_t s);
 void launch_link(const jfof_cells &c, const FofBuffers &fb, const LinkParams &lp, int32_t *label,

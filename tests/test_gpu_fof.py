@@ -87,19 +87,20 @@ def test_labels_invariant_across_grids(J, seed):
 
 
 @pytest.mark.parametrize("boost", [1.0, 2.5])
-def test_labels_invariant_across_dense_thresholds(J, boost):
-    # threshold 0 turns the sub-cell path off; 1 sends almost every cell through it
+def test_labels_invariant_across_cell_classes(J, boost):
+    # dense threshold 0 turns the sub-cell path off; 1 sends almost every cell
+    # through it; small threshold 0 sends every cell to the warp paths
     spec = synth.BoxSpec("t", 300_000, 67.0, synth.linking_length(67.0, 300_000) * boost, 1500, 0.6, 9)
     pos, _ = synth.generate(spec, device="cuda", velocities=False)
     pos_np = pos.cpu().numpy()
     lab_ref = oracle.fof_labels(pos_np, spec.L, spec.b)
     try:
-        for T in (0, 1, 8, 64, 1000):
-            J.set_dense_threshold(T)
+        for S, T in ((0, 0), (0, 1), (8, 0), (1, 8), (8, 64), (3, 12), (64, 1000), (100000, 0)):
+            J.set_cell_classes(S, T)
             _, r, H = run_fof(J, pos_np, spec.L, spec.b, spec.min_size)
-            assert np.array_equal(r.label.cpu().numpy(), lab_ref), T
+            assert np.array_equal(r.label.cpu().numpy(), lab_ref), (S, T)
     finally:
-        J.set_dense_threshold(64)
+        J.set_cell_classes(8, 64)
 
 
 def test_ragged_sizes_and_tiny_boxes(J):
