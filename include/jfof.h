@@ -201,6 +201,68 @@ int jfof_halo_props_backward(jfof_ctx *ctx, const float *vel, const int32_t *hal
                              const float *g_vmean, const float *g_sigv, float *g_pos,
                              float *g_vel);
 
+/* ---------------------------------------------------------------------- */
+/* REINFORCE topological mode (Sec. 3.2, Eqs. 6-8).                        */
+
+/* Host helper for the edge-probability constant `coef`:
+     prob_form 0: p = sigmoid((b - d) / tau), coef = 1/tau (tau <= 0 means
+                  tau = 0.05 b), computed in double and rounded once;
+     prob_form 1: p = sigmoid(alpha (b^2 - d^2) / b^2) (Eq. 8),
+                  coef = alpha / f32(b*b), computed in double, rounded once. */
+int jfof_prob_coef(float b, int32_t prob_form, float tau, float alpha, float *coef);
+
+/* a11: the fixed candidate list ("we do not rebuild the neighbor list",
+   Sec. 3.2): every unordered pair i < j with d2 < r_cut*r_cut (d2 as in
+   jfof_link), sorted by (i, j), with d = sqrt(d2) (IEEE) and the edge
+   probability p = 1 / (1 + E(-z)), z = (b - d)*coef (form 0) or
+   (b*b - d2)*coef (form 1); E is the library's binary32 exponential
+   (Cody-Waite reduction + degree-7 Taylor, see jfof_eval_exp).
+   Writes min(E, cap) pairs into pair_i/pair_j (int32) and pair_d/pair_p
+   (float32), and the total E into *n_pairs (device int64).  cap = 0 only
+   counts (the output pointers may then be NULL); E > cap > 0 latches
+   JFOF_EOVERFLOW and writes no pairs.  E must fit in uint32. */
+int jfof_pairs_bytes(int64_t N, float L, float r_cut, size_t *bytes);
+int jfof_pairs(jfof_ctx *ctx, const float *pos, int64_t N, float L, float b, float r_cut,
+               int32_t prob_form, float coef, uint32_t flags, void *ws, size_t ws_bytes,
+               int64_t cap, int32_t *pair_i, int32_t *pair_j, float *pair_d, float *pair_p,
+               int64_t *n_pairs);
+
+/* a12: K stochastic topologies in one call (Eq. 8 Bernoulli edges over the
+   fixed list).  Edge e is present in sample k iff u < p_e, where
+   u = (w >> 8) * 2^-24 and w is word (k mod 4) of Philox4x32-10 (Salmon et
+   al., SC'11) with key (seed low 32 bits, seed high 32 bits) and counter
+   (min(i,j), max(i,j), floor(k/4), 0).  Outputs: labels [K, N] device int32,
+   row k = smallest member index of each particle's component in sample k;
+   n_halos [K] device int32 = components with >= min_size members.  E is the
+   host pair count.  The pair arrays are from jfof_pairs. */
+int jfof_reinforce_sample_bytes(int64_t N, size_t *bytes);
+int jfof_reinforce_sample(jfof_ctx *ctx, int64_t N, const int32_t *pair_i, const int32_t *pair_j,
+                          const float *pair_p, int64_t E, int32_t K, uint64_t seed,
+                          int32_t min_size, void *ws, size_t ws_bytes, int32_t *labels,
+                          int32_t *n_halos);
+
+/* a13: score-function gradient with respect to positions (Eqs. 6-7):
+     g = (1/K) sum_k A_k d log p(y_k) / dx,  d log p / dz_e = y_e - p_e,
+   with y_ke regenerated from the same counter-based draws (no edge storage),
+   advantage A [K] device float32 (e.g. L_k - mean L, the batch-mean baseline
+   of Sec. 3.2), dz/dx_i = (x_j - x_i)_mi / (tau d) (form 0) or
+   2 (alpha/b^2) (x_j - x_i)_mi (form 1), dz/dx_j = -dz/dx_i, and 0 for d = 0.
+   Binary32 with compensated sums in a fixed order (deterministic).  The pairs
+   must be sorted by i (as jfof_pairs writes them).  g_pos: device [N,3]. */
+int jfof_reinforce_grad_bytes(int64_t N, int64_t E, size_t *bytes);
+int jfof_reinforce_grad(jfof_ctx *ctx, const float *pos, int64_t N, float L, uint32_t flags,
+                        const int32_t *pair_i, const int32_t *pair_j, const float *pair_d,
+                        const float *pair_p, int64_t E, int32_t K, uint64_t seed,
+                        const float *advantage, int32_t prob_form, float coef, void *ws,
+                        size_t ws_bytes, float *g_pos);
+
+/* Verification hooks: the device exponential E(x) used for edge
+   probabilities, y[t] = E(x[t]); and the edge uniforms of jfof_reinforce_sample,
+   u[t] for edge (i[t], j[t]) in sample k[t].  All arrays on the device. */
+int jfof_eval_exp(jfof_ctx *ctx, const float *x, float *y, int64_t n);
+int jfof_eval_edge_uniform(jfof_ctx *ctx, uint64_t seed, const int32_t *i, const int32_t *j,
+                           const int32_t *k, float *u, int64_t n);
+
 /* Convenience: a1-a7 in one call (bin, link, groups) with one workspace. */
 int jfof_fof_all_bytes(int64_t N, int32_t n_axis, size_t *bytes);
 int jfof_fof(jfof_ctx *ctx, const float *pos, int64_t N, float L, float b, int32_t n_axis,

@@ -265,3 +265,54 @@ def reinforce_grad(pos, L: float, pi, pj, pp, K: int, seed: int, adv, form: int,
     _load().orc_reinforce_grad(p, p.shape[0], np.float32(L), pi.shape[0], pi, pj, pp, K,
                                seed, a, form, float(coef), g)
     return g
+
+
+def _declare_extra(lib):
+    c = ctypes
+    lib.orc_reinforce_sample_one.restype = c.c_int
+    lib.orc_reinforce_sample_one.argtypes = [c.c_int64, c.c_int64, _i32p, _i32p, _f32p, c.c_int32,
+                                             c.c_uint64, c.c_int32, _i32p, c.POINTER(c.c_int32)]
+    lib.orc_reinforce_grad_masked.restype = c.c_int
+    lib.orc_reinforce_grad_masked.argtypes = [_f32p, c.c_int64, c.c_float, c.c_int64, _i32p, _i32p,
+                                              _f32p, c.c_int32, c.c_uint64, _f64p, c.c_int32,
+                                              c.c_double,
+                                              np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS"),
+                                              _f64p]
+    lib.orc_exp_array.restype = None
+    lib.orc_exp_array.argtypes = [_f32p, _f32p, c.c_int64]
+    return lib
+
+
+def reinforce_sample_one(N: int, pi, pj, pp, k: int, seed: int, min_size: int):
+    """Sample k alone: (labels[N], n_halos)."""
+    lib = _declare_extra(_load())
+    lab = np.empty(N, np.int32)
+    nh = ctypes.c_int32()
+    st = lib.orc_reinforce_sample_one(N, len(pi), np.ascontiguousarray(pi, np.int32),
+                                      np.ascontiguousarray(pj, np.int32),
+                                      np.ascontiguousarray(pp, np.float32), k, seed, min_size, lab,
+                                      ctypes.byref(nh))
+    if st != 0:
+        raise OracleError(f"orc_reinforce_sample_one status {st}")
+    return lab, nh.value
+
+
+def reinforce_grad_masked(pos, L: float, pi, pj, pp, K: int, seed: int, adv, form: int, coef: float,
+                          mask) -> np.ndarray:
+    """FP64 score-function gradient for the particles with mask != 0."""
+    lib = _declare_extra(_load())
+    p = _pos32(pos)
+    g = np.empty((p.shape[0], 3), np.float64)
+    lib.orc_reinforce_grad_masked(p, p.shape[0], np.float32(L), len(pi), np.ascontiguousarray(pi, np.int32),
+                                  np.ascontiguousarray(pj, np.int32), np.ascontiguousarray(pp, np.float32),
+                                  K, seed, np.ascontiguousarray(adv, np.float64), form, float(coef),
+                                  np.ascontiguousarray(mask, np.uint8), g)
+    return g
+
+
+def exp32_array(x) -> np.ndarray:
+    lib = _declare_extra(_load())
+    xa = np.ascontiguousarray(x, np.float32)
+    y = np.empty_like(xa)
+    lib.orc_exp_array(xa, y, xa.size)
+    return y

@@ -720,3 +720,74 @@ int orc_reinforce_grad(const float *pos, int64_t N, float L, int64_t E,
     (void)N;
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Helpers for checks at full size: the same definitions, restricted.        */
+
+/* Sample k alone (labels [N], smallest member index; *n_halos). */
+int orc_reinforce_sample_one(int64_t N, int64_t E, const int32_t *pi, const int32_t *pj,
+                             const float *pp, int32_t k, uint64_t seed, int32_t min_size,
+                             int32_t *lab, int32_t *n_halos)
+{
+    int64_t *cnt = (int64_t *)calloc((size_t)N, sizeof(int64_t));
+    if (!cnt)
+        return ORC_ENOMEM;
+    for (int64_t i = 0; i < N; ++i)
+        lab[i] = (int32_t)i;
+    for (int64_t e = 0; e < E; ++e)
+        if (orc_edge_uniform(seed, pi[e], pj[e], k) < pp[e])
+            uf_union(lab, pi[e], pj[e]);
+    for (int64_t i = 0; i < N; ++i)
+        lab[i] = uf_find(lab, (int32_t)i);
+    for (int64_t i = 0; i < N; ++i)
+        cnt[lab[i]] += 1;
+    int32_t h = 0;
+    for (int64_t i = 0; i < N; ++i)
+        if (lab[i] == i && cnt[i] >= min_size)
+            ++h;
+    *n_halos = h;
+    free(cnt);
+    return ORC_OK;
+}
+
+/* The score-function gradient of orc_reinforce_grad, evaluated only for the
+   particles with mask[i] != 0 (other rows are left 0). */
+int orc_reinforce_grad_masked(const float *pos, int64_t N, float L, int64_t E,
+                              const int32_t *pi, const int32_t *pj, const float *pp,
+                              int32_t K, uint64_t seed, const double *adv, int32_t form,
+                              double coef, const uint8_t *mask, double *g)
+{
+    for (int64_t i = 0; i < 3 * N; ++i)
+        g[i] = 0.0;
+    for (int64_t e = 0; e < E; ++e) {
+        int32_t i = pi[e], j = pj[e];
+        if (!mask[i] && !mask[j])
+            continue;
+        double s = 0.0;
+        for (int32_t k = 0; k < K; ++k) {
+            double y = orc_edge_uniform(seed, i, j, k) < pp[e] ? 1.0 : 0.0;
+            s += adv[k] * (y - (double)pp[e]);
+        }
+        s /= (double)K;
+        double dx[3], d2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            dx[a] = mi_f64((double)pos[3 * j + a] - (double)pos[3 * i + a], (double)L);
+            d2 += dx[a] * dx[a];
+        }
+        double fac = form == 0 ? (d2 > 0.0 ? coef / sqrt(d2) : 0.0) : 2.0 * coef;
+        for (int a = 0; a < 3; ++a) {
+            if (mask[i])
+                g[3 * i + a] += s * fac * dx[a];
+            if (mask[j])
+                g[3 * j + a] -= s * fac * dx[a];
+        }
+    }
+    return ORC_OK;
+}
+
+/* Element-wise orc_exp over an array. */
+void orc_exp_array(const float *x, float *y, int64_t n)
+{
+    for (int64_t t = 0; t < n; ++t)
+        y[t] = orc_exp(x[t]);
+}

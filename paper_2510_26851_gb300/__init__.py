@@ -28,6 +28,9 @@ EXPORTED = [
     "jfof_set_loop_budget", "jfof_set_cell_classes", "jfof_trace_enable", "jfof_trace_read", "jfof_max_cells_per_axis", "jfof_default_cells_per_axis",
     "jfof_fof_bytes", "jfof_bin_cells", "jfof_link", "jfof_groups_bytes", "jfof_groups",
     "jfof_halo_props", "jfof_halo_props_backward", "jfof_fof_all_bytes", "jfof_fof",
+    "jfof_prob_coef", "jfof_pairs_bytes", "jfof_pairs", "jfof_reinforce_sample_bytes",
+    "jfof_reinforce_sample", "jfof_reinforce_grad_bytes", "jfof_reinforce_grad", "jfof_eval_exp",
+    "jfof_eval_edge_uniform",
 ]
 
 
@@ -76,6 +79,16 @@ def _declare(lib):
         "jfof_halo_props_backward": [vp, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp],
         "jfof_fof_all_bytes": [i64, i32, P(sz)],
         "jfof_fof": [vp, vp, i64, f32, f32, i32, u32, i32, vp, sz, vp, vp, vp, vp, vp, vp],
+        "jfof_prob_coef": [f32, i32, f32, f32, P(f32)],
+        "jfof_pairs_bytes": [i64, f32, f32, P(sz)],
+        "jfof_pairs": [vp, vp, i64, f32, f32, f32, i32, f32, u32, vp, sz, i64, vp, vp, vp, vp, vp],
+        "jfof_reinforce_sample_bytes": [i64, P(sz)],
+        "jfof_reinforce_sample": [vp, i64, vp, vp, vp, i64, i32, c.c_uint64, i32, vp, sz, vp, vp],
+        "jfof_reinforce_grad_bytes": [i64, i64, P(sz)],
+        "jfof_reinforce_grad": [vp, vp, i64, f32, u32, vp, vp, vp, vp, i64, i32, c.c_uint64, vp, i32,
+                                f32, vp, sz, vp],
+        "jfof_eval_exp": [vp, vp, vp, i64],
+        "jfof_eval_edge_uniform": [vp, c.c_uint64, vp, vp, vp, vp, i64],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -380,3 +393,138 @@ class HaloProps(torch.autograd.Function):
         gp, gv = halo_props_backward(vel, g, vmean, sigv, pad(g_com, (Hc, 3)),
                                      pad(g_vmean, (Hc, 3)), pad(g_sigv, (Hc,)))
         return gp, gv, None, None, None
+
+
+# ---------------------------------------------------------------------------
+# REINFORCE topological mode (Sec. 3.2)
+
+def prob_coef(b: float, prob_form: int = 0, tau: float = 0.0, alpha: float = 0.5) -> float:
+    """Edge-probability constant: 1/tau (form 0, tau <= 0 -> 0.05 b) or alpha/b^2 (form 1)."""
+    c = ctypes.c_float()
+    _check(library().jfof_prob_coef(b, prob_form, tau, alpha, ctypes.byref(c)), "jfof_prob_coef")
+    return c.value
+
+
+@dataclass
+class Pairs:
+    i: torch.Tensor  # [E] int32, sorted by (i, j), i < j
+    j: torch.Tensor  # [E] int32
+    d: torch.Tensor  # [E] float32
+    p: torch.Tensor  # [E] float32
+    N: int
+    L: float
+    b: float
+    prob_form: int
+    coef: float
+    wrap: bool
+
+    @property
+    def E(self) -> int:
+        return int(self.i.shape[0])
+
+
+def pairs(pos: torch.Tensor, L: float, b: float, r_cut: float | None = None, prob_form: int = 0,
+          coef: float | None = None, wrap: bool = False) -> Pairs:
+    """a11: fixed candidate pairs within r_cut (default 1.5 b) with d and p.
+    Counts first, then allocates exactly and fills (one host sync)."""
+    _need(pos, torch.float32, None, "pos")
+    N = pos.shape[0]
+    dev = pos.device
+    if r_cut is None:
+        r_cut = float(torch.tensor(1.5 * float(torch.tensor(b, dtype=torch.float32)),
+                                   dtype=torch.float32).item())
+    if coef is None:
+        coef = prob_coef(b, prob_form)
+    s = ctypes.c_size_t()
+    _check(library().jfof_pairs_bytes(N, L, r_cut, ctypes.byref(s)), "jfof_pairs_bytes")
+    ws = _ws(s.value, dev)
+    nE = torch.zeros(1, dtype=torch.int64, device=dev)
+    h = context(dev)
+    flags = JFOF_WRAP if wrap else 0
+    _check(library().jfof_pairs(h, _ptr(pos), N, L, b, r_cut, prob_form, coef, flags, _ptr(ws),
+                                ws.numel(), 0, None, None, None, None, _ptr(nE)), "jfof_pairs")
+    sync(dev)
+    E = int(nE.item())
+    out = Pairs(torch.empty(E, dtype=torch.int32, device=dev), torch.empty(E, dtype=torch.int32, device=dev),
+                torch.empty(E, device=dev), torch.empty(E, device=dev), N, L, b, prob_form, coef, wrap)
+    if E:
+        _check(library().jfof_pairs(h, _ptr(pos), N, L, b, r_cut, prob_form, coef, flags, _ptr(ws),
+                                    ws.numel(), E, _ptr(out.i), _ptr(out.j), _ptr(out.d), _ptr(out.p),
+                                    _ptr(nE)), "jfof_pairs")
+    return out
+
+
+def reinforce_sample(pr: Pairs, K: int, seed: int, min_size: int = 20,
+                     labels: torch.Tensor | None = None):
+    """a12: labels [K, N] (smallest member index per sample) and n_halos [K]."""
+    dev = pr.i.device
+    N = pr.N
+    if labels is None:
+        labels = torch.empty(K, N, dtype=torch.int32, device=dev)
+    _need(labels, torch.int32, (K, N), "labels")
+    nh = torch.empty(K, dtype=torch.int32, device=dev)
+    s = ctypes.c_size_t()
+    _check(library().jfof_reinforce_sample_bytes(N, ctypes.byref(s)), "jfof_reinforce_sample_bytes")
+    ws = _ws(s.value, dev)
+    _check(library().jfof_reinforce_sample(context(dev), N, _ptr(pr.i), _ptr(pr.j), _ptr(pr.p), pr.E, K,
+                                           ctypes.c_uint64(seed), min_size, _ptr(ws), ws.numel(),
+                                           _ptr(labels), _ptr(nh)), "jfof_reinforce_sample")
+    return labels, nh
+
+
+def reinforce_grad(pos: torch.Tensor, pr: Pairs, K: int, seed: int, advantage: torch.Tensor) -> torch.Tensor:
+    """a13: score-function gradient w.r.t. positions, [N,3]."""
+    _need(pos, torch.float32, None, "pos")
+    _need(advantage, torch.float32, (K,), "advantage")
+    dev = pos.device
+    N = pos.shape[0]
+    s = ctypes.c_size_t()
+    _check(library().jfof_reinforce_grad_bytes(N, pr.E, ctypes.byref(s)), "jfof_reinforce_grad_bytes")
+    ws = _ws(s.value, dev)
+    g = torch.empty(N, 3, device=dev)
+    _check(library().jfof_reinforce_grad(context(dev), _ptr(pos), N, pr.L, JFOF_WRAP if pr.wrap else 0,
+                                         _ptr(pr.i), _ptr(pr.j), _ptr(pr.d), _ptr(pr.p), pr.E, K,
+                                         ctypes.c_uint64(seed), _ptr(advantage), pr.prob_form, pr.coef,
+                                         _ptr(ws), ws.numel(), _ptr(g)), "jfof_reinforce_grad")
+    return g
+
+
+def eval_exp(x: torch.Tensor) -> torch.Tensor:
+    _need(x, torch.float32, None, "x")
+    y = torch.empty_like(x)
+    _check(library().jfof_eval_exp(context(x.device), _ptr(x), _ptr(y), x.numel()), "jfof_eval_exp")
+    return y
+
+
+def eval_edge_uniform(seed: int, i: torch.Tensor, j: torch.Tensor, k: torch.Tensor) -> torch.Tensor:
+    for t, nm in ((i, "i"), (j, "j"), (k, "k")):
+        _need(t, torch.int32, None, nm)
+    u = torch.empty(i.shape, device=i.device)
+    _check(library().jfof_eval_edge_uniform(context(i.device), ctypes.c_uint64(seed), _ptr(i), _ptr(j),
+                                            _ptr(k), _ptr(u), i.numel()), "jfof_eval_edge_uniform")
+    return u
+
+
+class ReinforceFoF(torch.autograd.Function):
+    """Expected loss over stochastic FoF topologies (Sec. 3.2, Eqs. 6-8).
+
+    forward(pos, pairs, losses, seed) -> mean of the per-sample losses
+    ``losses`` [K] (computed by the caller from the labels of
+    ``reinforce_sample(pairs, K, seed)``); backward returns the REINFORCE
+    gradient with the batch-mean baseline, A_k = L_k - mean(L).  The pair
+    list (the neighbour structure) is fixed, as in the paper.
+    """
+
+    @staticmethod
+    def forward(ctx, pos, pr: Pairs, losses, seed: int):
+        lo = losses.detach().to(torch.float32).contiguous()
+        ctx.pr, ctx.seed = pr, seed
+        ctx.save_for_backward(pos.detach(), lo)
+        return lo.mean()
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        pos, lo = ctx.saved_tensors
+        adv = (lo - lo.mean()).contiguous()
+        g = reinforce_grad(pos.contiguous(), ctx.pr, lo.shape[0], ctx.seed, adv)
+        return g * grad_out, None, None, None
