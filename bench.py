@@ -171,6 +171,70 @@ def run_reference(args, rank, world):
     return 0
 
 
+def _events_ms(fn, reps):
+    s = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    for _ in range(reps):
+        fn()
+    b.record(s)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def measure_batched(J, reps=3):
+    """64 uneven boxes: one CUDA-graph launch vs the per-box loop."""
+    specs = synth.batch_specs()
+    parts = [synth.generate(sp, device="cuda", velocities=False)[0] for sp in specs]
+    pos = torch.cat(parts).contiguous()
+    del parts
+    import numpy as np
+    off = np.concatenate([[0], np.cumsum([sp.N for sp in specs])]).astype(np.int64)
+    bt = J.Batch(off, [s.L for s in specs], [s.b for s in specs], min_size=20)
+    for _ in range(2):
+        bt.run(pos, use_graph=True)
+        bt.run(pos, use_graph=False)
+    J.sync()
+    g_ms = _events_ms(lambda: bt.run(pos, use_graph=True), reps)
+    l_ms = _events_ms(lambda: bt.run(pos, use_graph=False), reps)
+    J.sync()
+    N = int(off[-1])
+    return {"workload": "64 boxes, N log-uniform in [32^3, 192^3], L in [50, 400], seeds 0-63",
+            "particles": N, "graph_ms": g_ms, "loop_ms": l_ms, "speedup_vs_loop": l_ms / g_ms,
+            "value": N / (g_ms * 1e-3), "unit": UNIT}
+
+
+def measure_differentiable(J, reps=3):
+    """128^3 box: frozen-assignment forward/backward props and REINFORCE."""
+    spec = synth.DIFF_128
+    pos, vel = synth.generate(spec, device="cuda")
+    r = J.fof(pos, spec.L, spec.b, spec.min_size)
+    p = J.halo_props(pos, vel, spec.L, r.groups)
+    J.sync()
+    H = r.groups.n_halos
+    w = torch.rand(H, device="cuda", generator=torch.Generator(device="cuda").manual_seed(1))
+    g_com = torch.zeros(r.groups.H_cap, 3, device="cuda")
+    g_sig = torch.zeros(r.groups.H_cap, device="cuda")
+    g_com[:H] = 2 * w[:, None] * p.com[:H]
+    g_sig[:H] = 2 * w * p.sigv[:H]
+    fwd = _events_ms(lambda: J.halo_props(pos, vel, spec.L, r.groups, out=p), reps)
+    bwd = _events_ms(lambda: J.halo_props_backward(vel, r.groups, p.vmean, p.sigv, g_com=g_com, g_sigv=g_sig),
+                     reps)
+    pr = J.pairs(pos, spec.L, spec.b)
+    K = 256
+    labels = torch.empty(K, spec.N, dtype=torch.int32, device="cuda")
+    t_pairs = _events_ms(lambda: J.pairs(pos, spec.L, spec.b), 1)
+    t_samp = _events_ms(lambda: J.reinforce_sample(pr, K, 0, spec.min_size, labels=labels), reps)
+    _, nh = J.reinforce_sample(pr, K, 0, spec.min_size, labels=labels)
+    adv = (nh.float() - nh.float().mean()).contiguous()
+    t_grad = _events_ms(lambda: J.reinforce_grad(pos, pr, K, 0, adv), reps)
+    J.sync()
+    return {"workload": "128^3 box, L=200, b=0.3125", "halos": H,
+            "props_fwd_ms": fwd, "props_bwd_ms": bwd, "bwd_over_fwd": bwd / fwd,
+            "reinforce": {"pairs": pr.E, "K": K, "pairs_ms": t_pairs, "sample_ms": t_samp,
+                          "grad_ms": t_grad, "samples_per_s": K / (t_samp * 1e-3)}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -179,6 +243,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="1024", choices=["1024", "256"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and differentiable lines")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -303,6 +368,19 @@ def main():
         except Exception as e:  # the oracle is a reported baseline, never the product
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
 
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        del ws, res, props
+        torch.cuda.empty_cache()
+        try:
+            extras["batched"] = measure_batched(J)
+        except Exception as e:  # reported, never hidden
+            extras["batched"] = {"error": str(e)}
+        try:
+            extras["differentiable"] = measure_differentiable(J)
+        except Exception as e:
+            extras["differentiable"] = {"error": str(e)}
+
     if rank == 0:
         launches = sum(c for c, _ in trace.values()) // args.steps
         line = {
@@ -316,6 +394,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": launches * args.steps, "kernels": kernels,
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

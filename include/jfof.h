@@ -263,6 +263,43 @@ int jfof_eval_exp(jfof_ctx *ctx, const float *x, float *y, int64_t n);
 int jfof_eval_edge_uniform(jfof_ctx *ctx, uint64_t seed, const int32_t *i, const int32_t *j,
                            const int32_t *k, float *u, int64_t n);
 
+/* ---------------------------------------------------------------------- */
+/* Batched FoF: many independent boxes (no counterpart in the paper; its   */
+/* AI-systems form of Sec. 1's GPU-resident analysis).                     */
+
+/* Bytes of workspace for jfof_fof_batched.  h_box_offset: host [B+1], box k
+   holds particles [h_box_offset[k], h_box_offset[k+1]) of the concatenated
+   arrays (h_box_offset[0] = 0, total <= 2^31-1); h_L, h_b: host [B];
+   h_n_axis: host [B] cells per axis (0 or NULL = default). */
+int jfof_batch_bytes(const int64_t *h_box_offset, int32_t B, const float *h_L, const float *h_b,
+                     const int32_t *h_n_axis, int32_t min_size, size_t *bytes);
+
+/* a1-a7 for B boxes: labels (smallest member index, numbered inside each
+   box), halo ids (numbered from 0 inside each box, -1 below min_size) and
+   n_halos [B], all device arrays over the concatenated particles.  Boxes
+   never interact.  h_small / h_dense: host [B] per-box cell classes (NULL =
+   the context's).  use_graph != 0: the first call captures every box's
+   pipeline as a parallel branch of one CUDA graph and later calls with the
+   same configuration (pointers, sizes, parameters, stream) replay it with a
+   single launch; use_graph = 0 enqueues the boxes one after another (the
+   per-box loop).  Capturing requires that the context's stream is not itself
+   being captured. */
+int jfof_fof_batched(jfof_ctx *ctx, const float *pos, const int64_t *h_box_offset, int32_t B,
+                     const float *h_L, const float *h_b, const int32_t *h_n_axis,
+                     const int32_t *h_small, const int32_t *h_dense, uint32_t flags,
+                     int32_t min_size, void *ws, size_t ws_bytes, int32_t *label,
+                     int32_t *halo_id, int32_t *n_halos, int32_t use_graph);
+
+/* Autotuner: times the a1-a7 pipeline on one box for candidate grids (the
+   default n and n scaled by 0.8 and 1.26, where the workspace fits) and cell
+   classes, `reps` runs each after a warm-up, and returns the fastest choice
+   (*best_n_axis, *best_small, *best_dense) and its time in ms.  Synchronises.
+   Outputs label/halo_id [N] and n_halos [1] are scratch for the trials. */
+int jfof_autotune(jfof_ctx *ctx, const float *pos, int64_t N, float L, float b, uint32_t flags,
+                  int32_t min_size, void *ws, size_t ws_bytes, int32_t *label, int32_t *halo_id,
+                  int32_t *n_halos, int32_t reps, int32_t *best_n_axis, int32_t *best_small,
+                  int32_t *best_dense, float *best_ms);
+
 /* Convenience: a1-a7 in one call (bin, link, groups) with one workspace. */
 int jfof_fof_all_bytes(int64_t N, int32_t n_axis, size_t *bytes);
 int jfof_fof(jfof_ctx *ctx, const float *pos, int64_t N, float L, float b, int32_t n_axis,

@@ -30,7 +30,7 @@ EXPORTED = [
     "jfof_halo_props", "jfof_halo_props_backward", "jfof_fof_all_bytes", "jfof_fof",
     "jfof_prob_coef", "jfof_pairs_bytes", "jfof_pairs", "jfof_reinforce_sample_bytes",
     "jfof_reinforce_sample", "jfof_reinforce_grad_bytes", "jfof_reinforce_grad", "jfof_eval_exp",
-    "jfof_eval_edge_uniform",
+    "jfof_eval_edge_uniform", "jfof_batch_bytes", "jfof_fof_batched", "jfof_autotune",
 ]
 
 
@@ -89,6 +89,10 @@ def _declare(lib):
                                 f32, vp, sz, vp],
         "jfof_eval_exp": [vp, vp, vp, i64],
         "jfof_eval_edge_uniform": [vp, c.c_uint64, vp, vp, vp, vp, i64],
+        "jfof_batch_bytes": [vp, i32, vp, vp, vp, i32, P(sz)],
+        "jfof_fof_batched": [vp, vp, vp, i32, vp, vp, vp, vp, vp, u32, i32, vp, sz, vp, vp, vp, i32],
+        "jfof_autotune": [vp, vp, i64, f32, f32, u32, i32, vp, sz, vp, vp, vp, i32, P(i32), P(i32),
+                          P(i32), P(f32)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -528,3 +532,67 @@ class ReinforceFoF(torch.autograd.Function):
         adv = (lo - lo.mean()).contiguous()
         g = reinforce_grad(pos.contiguous(), ctx.pr, lo.shape[0], ctx.seed, adv)
         return g * grad_out, None, None, None
+
+
+# ---------------------------------------------------------------------------
+# Batched boxes and the autotuner
+
+class Batch:
+    """Many independent boxes through one CUDA-graph launch (or the per-box
+    loop with ``use_graph=False``).  Host-side sizes and parameters are fixed
+    at construction; inputs and outputs are device tensors over the
+    concatenated particles."""
+
+    def __init__(self, box_offset, L, b, min_size: int = 20, n_axis=None, small=None, dense=None,
+                 device=None):
+        import numpy as _np
+        self.off = _np.ascontiguousarray(box_offset, _np.int64)
+        self.B = len(self.off) - 1
+        self.L = _np.ascontiguousarray(L, _np.float32)
+        self.b = _np.ascontiguousarray(b, _np.float32)
+        self.n = None if n_axis is None else _np.ascontiguousarray(n_axis, _np.int32)
+        self.small = None if small is None else _np.ascontiguousarray(small, _np.int32)
+        self.dense = None if dense is None else _np.ascontiguousarray(dense, _np.int32)
+        self.min_size = min_size
+        dev = torch.device("cuda") if device is None else torch.device(device)
+        s = ctypes.c_size_t()
+        _check(library().jfof_batch_bytes(self.off.ctypes.data, self.B, self.L.ctypes.data,
+                                          self.b.ctypes.data, None if self.n is None else self.n.ctypes.data,
+                                          min_size, ctypes.byref(s)), "jfof_batch_bytes")
+        self.ws = _ws(s.value, dev)
+        N = int(self.off[-1])
+        self.label = torch.empty(N, dtype=torch.int32, device=dev)
+        self.halo_id = torch.empty(N, dtype=torch.int32, device=dev)
+        self.n_halos = torch.empty(self.B, dtype=torch.int32, device=dev)
+
+    def run(self, pos: torch.Tensor, use_graph: bool = True, wrap: bool = False):
+        _need(pos, torch.float32, (int(self.off[-1]), 3), "pos")
+        arr = lambda a: None if a is None else a.ctypes.data  # noqa: E731
+        _check(library().jfof_fof_batched(
+            context(pos.device), _ptr(pos), self.off.ctypes.data, self.B, self.L.ctypes.data,
+            self.b.ctypes.data, arr(self.n), arr(self.small), arr(self.dense), JFOF_WRAP if wrap else 0,
+            self.min_size, _ptr(self.ws), self.ws.numel(), _ptr(self.label), _ptr(self.halo_id),
+            _ptr(self.n_halos), 1 if use_graph else 0), "jfof_fof_batched")
+        return self.label, self.halo_id, self.n_halos
+
+
+def autotune(pos: torch.Tensor, L: float, b: float, min_size: int = 20, reps: int = 2,
+             wrap: bool = False):
+    """Fastest (n_axis, small, dense, ms) for this box among the candidates."""
+    _need(pos, torch.float32, None, "pos")
+    N = pos.shape[0]
+    dev = pos.device
+    n0 = default_cells_per_axis(N, L, b)
+    nmax = max_cells_per_axis(L, b)
+    n_big = min(nmax, int(n0 * 1.26))
+    size = max(fof_all_bytes(N, n0), fof_all_bytes(N, max(3, n_big))) + 3 * 4 * N + (1 << 20)
+    ws = _ws(size, dev)
+    label = torch.empty(N, dtype=torch.int32, device=dev)
+    hid = torch.empty(N, dtype=torch.int32, device=dev)
+    nh = torch.empty(1, dtype=torch.int32, device=dev)
+    bn, bs, bd, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    _check(library().jfof_autotune(context(dev), _ptr(pos), N, L, b, JFOF_WRAP if wrap else 0, min_size,
+                                   _ptr(ws), ws.numel(), _ptr(label), _ptr(hid), _ptr(nh), reps,
+                                   ctypes.byref(bn), ctypes.byref(bs), ctypes.byref(bd), ctypes.byref(ms)),
+           "jfof_autotune")
+    return bn.value, bs.value, bd.value, ms.value

@@ -8,7 +8,7 @@
 
 using namespace jfof;
 
-namespace {
+namespace jfof {
 
 constexpr int32_t kMaxCellsPerAxis = 1600;
 
@@ -42,6 +42,10 @@ int resolve_n(int64_t N, float L, float b, int32_t n_axis, int32_t *out) {
     *out = n_axis;
     return JFOF_OK;
 }
+
+}  // namespace jfof
+
+namespace {
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? JFOF_OK : JFOF_ECUDA; }
 
@@ -105,6 +109,7 @@ int jfof_create(jfof_ctx **ctx, int device, void *stream) {
     jfof_ctx *c = new jfof_ctx();
     c->device = device;
     c->tracer = nullptr;
+    c->batch = nullptr;
     c->stream = reinterpret_cast<cudaStream_t>(stream);
     c->loop_budget = kDefaultLoopBudget;
     c->dense_threshold = kDefaultDenseThreshold;
@@ -134,6 +139,7 @@ int jfof_destroy(jfof_ctx *ctx) {
     jfof_trace_enable(ctx, 0);
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    destroy_batch_cache(ctx->batch);
     cudaFree(ctx->d_status);
     cudaFreeHost(ctx->h_status);
     delete ctx;

@@ -1,0 +1,304 @@
+// api_batch.cu -- a10: many independent boxes of uneven size in one CUDA-graph
+// launch (each box's bin/link/groups pipeline on its own stream branch, so
+// small boxes and the narrow phases of large ones overlap), the per-box loop
+// it is compared with, and the cell-class autotuner.
+#include <cstring>
+#include <vector>
+
+#include "jfof_internal.cuh"
+#include "k_fof.cuh"
+
+using namespace jfof;
+
+namespace jfof {
+
+// One box: bin, link and groups on stream s, all buffers in ws.
+struct BoxPlan {
+    int64_t N;
+    float L, b;
+    int n;
+    LinkParams lp;
+    int64_t H_cap;
+    size_t ws_off, fof_bytes, grp_bytes;
+    size_t count_off, start_off, members_off, total;
+};
+
+static BoxPlan plan_box(int64_t N, float L, float b, int n, int S, int T, int min_size) {
+    BoxPlan p{};
+    p.N = N;
+    p.L = L;
+    p.b = b;
+    p.n = n;
+    p.lp = make_link_params(N, L, b, n, S, T);
+    p.H_cap = N / min_size > 0 ? N / min_size : 1;
+    p.fof_bytes = fof_layout(N, n, nullptr, nullptr);
+    p.grp_bytes = groups_layout(N, p.H_cap, nullptr, nullptr);
+    p.count_off = p.fof_bytes + p.grp_bytes;
+    p.start_off = p.count_off + align_up(sizeof(int32_t) * size_t(p.H_cap));
+    p.members_off = p.start_off + align_up(sizeof(int32_t) * size_t(p.H_cap + 1));
+    p.total = p.members_off + align_up(sizeof(int32_t) * size_t(N));
+    return p;
+}
+
+static void run_box(const BoxPlan &p, const float *pos, uint32_t flags, int min_size, char *ws, int32_t *label,
+                    int32_t *halo_id, int32_t *n_halos, const DevStatus &st, cudaStream_t s) {
+    FofBuffers fb;
+    fof_layout(p.N, p.n, &fb, ws);
+    launch_bin_cells(pos, p.N, p.L, p.n, (flags & JFOF_WRAP) != 0, p.lp, fb, st, s);
+    jfof_cells c{};
+    c.n = p.N;
+    c.n_axis = p.n;
+    c.brick = kBrick;
+    c.L = p.L;
+    c.b = p.b;
+    c.flags = flags;
+    c.small_threshold = p.lp.S;
+    c.dense_threshold = p.lp.T;
+    c.spos = fb.spos;
+    c.cell_start = fb.cell_start;
+    c.n_cells_table = cell_table_entries(p.n);
+    c.workspace = ws;
+    launch_link(c, fb, p.lp, label, st, s);
+    GroupBuffers gb;
+    groups_layout(p.N, p.H_cap, &gb, ws + p.fof_bytes);
+    launch_groups(label, p.N, min_size, p.H_cap, gb, halo_id, reinterpret_cast<int32_t *>(ws + p.count_off),
+                  reinterpret_cast<int32_t *>(ws + p.start_off), reinterpret_cast<int32_t *>(ws + p.members_off),
+                  n_halos, st, s);
+}
+
+// Cached graph of the last batch configuration.
+struct BatchCache {
+    std::vector<int64_t> off;
+    std::vector<float> L, b;
+    std::vector<int> n, S, T;
+    const void *pos = nullptr, *ws = nullptr, *label = nullptr, *halo_id = nullptr, *n_halos = nullptr;
+    uint32_t flags = 0;
+    int min_size = 0;
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaStream_t> streams;  // [0] capture origin, [1..B] box branches
+    std::vector<cudaEvent_t> events;    // [0] fork, [1..B] joins
+    ~BatchCache() {
+        if (exec) cudaGraphExecDestroy(exec);
+        for (auto s : streams) cudaStreamDestroy(s);
+        for (auto e : events) cudaEventDestroy(e);
+    }
+};
+
+void destroy_batch_cache(BatchCache *c) { delete c; }
+
+void ensure_link_tables();
+
+}  // namespace jfof
+
+namespace {
+
+struct BatchArgs {
+    int64_t total_N;
+    std::vector<BoxPlan> boxes;
+    size_t ws_bytes;
+};
+
+int plan_batch(const int64_t *h_off, int32_t B, const float *h_L, const float *h_b, const int32_t *h_n,
+               const int32_t *h_S, const int32_t *h_T, int S_def, int T_def, int min_size, BatchArgs *out) {
+    if (!h_off || B < 1 || !h_L || !h_b || min_size < 1 || h_off[0] != 0) return JFOF_EINVAL;
+    out->boxes.clear();
+    size_t off = 0;
+    for (int k = 0; k < B; ++k) {
+        int64_t N = h_off[k + 1] - h_off[k];
+        int e = check_box(N, h_L[k], h_b[k]);
+        if (e) return e;
+        int32_t n;
+        if ((e = resolve_n(N, h_L[k], h_b[k], h_n ? h_n[k] : 0, &n))) return e;
+        BoxPlan p = plan_box(N, h_L[k], h_b[k], n, h_S ? h_S[k] : S_def, h_T ? h_T[k] : T_def, min_size);
+        p.ws_off = off;
+        off += align_up(p.total);
+        out->boxes.push_back(p);
+    }
+    out->total_N = h_off[B];
+    if (out->total_N > int64_t(INT32_MAX)) return JFOF_EINVAL;
+    out->ws_bytes = off;
+    return JFOF_OK;
+}
+
+bool same_config(const BatchCache &c, const BatchArgs &a, const int64_t *h_off, int32_t B, const float *pos,
+                 const void *ws, const int32_t *label, const int32_t *halo_id, const int32_t *n_halos,
+                 uint32_t flags, int min_size, cudaStream_t stream) {
+    if (!c.exec || int(c.n.size()) != B || c.pos != pos || c.ws != ws || c.label != label ||
+        c.halo_id != halo_id || c.n_halos != n_halos || c.flags != flags || c.min_size != min_size ||
+        c.stream != stream)
+        return false;
+    for (int k = 0; k < B; ++k) {
+        const BoxPlan &p = a.boxes[k];
+        if (c.off[k + 1] != h_off[k + 1] || c.L[k] != p.L || c.b[k] != p.b || c.n[k] != p.n || c.S[k] != p.lp.S ||
+            c.T[k] != p.lp.T)
+            return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int jfof_batch_bytes(const int64_t *h_box_offset, int32_t B, const float *h_L, const float *h_b,
+                     const int32_t *h_n_axis, int32_t min_size, size_t *bytes) {
+    if (!bytes) return JFOF_EINVAL;
+    BatchArgs a;
+    int e = plan_batch(h_box_offset, B, h_L, h_b, h_n_axis, nullptr, nullptr, 8, 64, min_size, &a);
+    if (e) return e;
+    *bytes = a.ws_bytes;
+    return JFOF_OK;
+}
+
+int jfof_fof_batched(jfof_ctx *ctx, const float *pos, const int64_t *h_box_offset, int32_t B, const float *h_L,
+                     const float *h_b, const int32_t *h_n_axis, const int32_t *h_small, const int32_t *h_dense,
+                     uint32_t flags, int32_t min_size, void *ws, size_t ws_bytes, int32_t *label,
+                     int32_t *halo_id, int32_t *n_halos, int32_t use_graph) {
+    if (!ctx || !pos || !ws || !label || !halo_id || !n_halos) return JFOF_EINVAL;
+    BatchArgs a;
+    int e = plan_batch(h_box_offset, B, h_L, h_b, h_n_axis, h_small, h_dense, ctx->small_threshold,
+                       ctx->dense_threshold, min_size, &a);
+    if (e) return e;
+    if (ws_bytes < a.ws_bytes) return JFOF_ENOMEM;
+    cudaSetDevice(ctx->device);
+    ensure_link_tables();
+    char *base = reinterpret_cast<char *>(ws);
+    DevStatus st = ctx->dev();
+    if (!use_graph) {
+        CtxScope scope(ctx);
+        for (int k = 0; k < B; ++k) {
+            const BoxPlan &p = a.boxes[k];
+            int64_t o = h_box_offset[k];
+            run_box(p, pos + 3 * o, flags, min_size, base + p.ws_off, label + o, halo_id + o, n_halos + k, st,
+                    ctx->stream);
+        }
+        return cudaGetLastError() == cudaSuccess ? JFOF_OK : JFOF_ECUDA;
+    }
+    if (!ctx->batch) ctx->batch = new BatchCache();
+    BatchCache &c = *ctx->batch;
+    if (!same_config(c, a, h_box_offset, B, pos, ws, label, halo_id, n_halos, flags, min_size, ctx->stream)) {
+        if (c.exec) {
+            cudaGraphExecDestroy(c.exec);
+            c.exec = nullptr;
+        }
+        while (int(c.streams.size()) < B + 1) {
+            cudaStream_t s;
+            if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return JFOF_ECUDA;
+            c.streams.push_back(s);
+        }
+        while (int(c.events.size()) < B + 1) {
+            cudaEvent_t ev;
+            if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return JFOF_ECUDA;
+            c.events.push_back(ev);
+        }
+        // capture on a library-owned stream (the caller's may be the legacy
+        // default stream, which cannot be captured): fork, one branch per box,
+        // join; the graph is then launched on the caller's stream
+        cudaStream_t origin = c.streams[0];
+        jfof::t_tracer = nullptr;
+        if (cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return JFOF_ECUDA;
+        cudaEventRecord(c.events[0], origin);
+        for (int k = 0; k < B; ++k) {
+            const BoxPlan &p = a.boxes[k];
+            int64_t o = h_box_offset[k];
+            cudaStreamWaitEvent(c.streams[k + 1], c.events[0], 0);
+            run_box(p, pos + 3 * o, flags, min_size, base + p.ws_off, label + o, halo_id + o, n_halos + k, st,
+                    c.streams[k + 1]);
+            cudaEventRecord(c.events[k + 1], c.streams[k + 1]);
+            cudaStreamWaitEvent(origin, c.events[k + 1], 0);
+        }
+        cudaGraph_t graph;
+        if (cudaStreamEndCapture(origin, &graph) != cudaSuccess) return JFOF_ECUDA;
+        cudaError_t ie = cudaGraphInstantiate(&c.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) {
+            c.exec = nullptr;
+            return JFOF_ECUDA;
+        }
+        c.off.assign(h_box_offset, h_box_offset + B + 1);
+        c.L.clear();
+        c.b.clear();
+        c.n.clear();
+        c.S.clear();
+        c.T.clear();
+        for (auto &p : a.boxes) {
+            c.L.push_back(p.L);
+            c.b.push_back(p.b);
+            c.n.push_back(p.n);
+            c.S.push_back(p.lp.S);
+            c.T.push_back(p.lp.T);
+        }
+        c.pos = pos;
+        c.ws = ws;
+        c.label = label;
+        c.halo_id = halo_id;
+        c.n_halos = n_halos;
+        c.flags = flags;
+        c.min_size = min_size;
+        c.stream = ctx->stream;
+    }
+    return cudaGraphLaunch(c.exec, ctx->stream) == cudaSuccess ? JFOF_OK : JFOF_ECUDA;
+}
+
+// Autotuner: times jfof_fof-equivalent runs of one box for candidate cell
+// classes (S, T) and grids n (those whose workspace fits ws), `reps` runs
+// each after one warm-up, and returns the fastest.  Synchronises.  Labels do
+// not depend on the choice.
+int jfof_autotune(jfof_ctx *ctx, const float *pos, int64_t N, float L, float b, uint32_t flags, int32_t min_size,
+                  void *ws, size_t ws_bytes, int32_t *label, int32_t *halo_id, int32_t *n_halos, int32_t reps,
+                  int32_t *best_n_axis, int32_t *best_small, int32_t *best_dense, float *best_ms) {
+    if (!ctx || !pos || !ws || !label || !halo_id || !n_halos || !best_n_axis || !best_small || !best_dense ||
+        reps < 1)
+        return JFOF_EINVAL;
+    int e = check_box(N, L, b);
+    if (e) return e;
+    int32_t n0;
+    if ((e = resolve_n(N, L, b, 0, &n0))) return e;
+    int32_t nmax = max_cells(L, b);
+    std::vector<int> ns = {n0};
+    for (double f : {0.8, 1.26}) {
+        int n = int(n0 * f);
+        if (n >= 3 && n <= nmax && n != n0) ns.push_back(n);
+    }
+    const int cls[][2] = {{8, 64}, {4, 64}, {8, 128}, {16, 64}, {8, 32}, {4, 96}};
+    cudaSetDevice(ctx->device);
+    ensure_link_tables();
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    float best = 1e30f;
+    DevStatus st = ctx->dev();
+    for (int n : ns) {
+        for (auto &c : cls) {
+            BoxPlan p = plan_box(N, L, b, n, c[0], c[1], min_size);
+            if (p.total > ws_bytes) continue;
+            run_box(p, pos, flags, min_size, reinterpret_cast<char *>(ws), label, halo_id, n_halos, st, ctx->stream);
+            cudaEventRecord(t0, ctx->stream);
+            for (int r = 0; r < reps; ++r)
+                run_box(p, pos, flags, min_size, reinterpret_cast<char *>(ws), label, halo_id, n_halos, st,
+                        ctx->stream);
+            cudaEventRecord(t1, ctx->stream);
+            if (cudaEventSynchronize(t1) != cudaSuccess) {
+                cudaEventDestroy(t0);
+                cudaEventDestroy(t1);
+                return JFOF_ECUDA;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, t0, t1);
+            ms /= reps;
+            if (ms < best) {
+                best = ms;
+                *best_n_axis = n;
+                *best_small = c[0];
+                *best_dense = c[1];
+            }
+        }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (best_ms) *best_ms = best;
+    return best < 1e30f ? JFOF_OK : JFOF_ENOMEM;
+}
+
+}  // extern "C"

@@ -239,9 +239,10 @@ inline int64_t cell_table_entries(int n) {
 }  // namespace jfof
 
 // Context (opaque in the C ABI).
-namespace jfof { struct Tracer; }
+namespace jfof { struct Tracer; struct BatchCache; void destroy_batch_cache(BatchCache *); }
 struct jfof_ctx {
     jfof::Tracer *tracer; // null unless tracing is on
+    jfof::BatchCache *batch; // cached graph of the last batched call
     int device;
     cudaStream_t stream;
     int *d_status;       // device status word

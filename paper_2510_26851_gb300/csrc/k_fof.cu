@@ -737,10 +737,14 @@ __global__ void __launch_bounds__(256) finalize_labels_kernel(const float4 *__re
 }
 
 // ---------------------------------------------------------------------------
-static bool g_sub62_ready = false;
+static bool g_sub62_ready[64] = {};
 
-static void ensure_sub_offsets() {
-    if (g_sub62_ready) return;
+// Fills the constant sub-cell offset table of the current device (a
+// synchronous copy: call outside stream capture).
+void ensure_link_tables() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || g_sub62_ready[dev]) return;
     int8_t t[62][3];
     int c = 0;
     for (int pass = 0; pass < 2; ++pass)
@@ -756,7 +760,7 @@ static void ensure_sub_offsets() {
                     ++c;
                 }
     cudaMemcpyToSymbol(c_sub62, t, sizeof(t));
-    g_sub62_ready = true;
+    g_sub62_ready[dev] = true;
 }
 
 LinkParams make_link_params(int64_t N, float L, float b, int n, int S, int T) {
@@ -779,7 +783,7 @@ LinkParams make_link_params(int64_t N, float L, float b, int n, int S, int T) {
 void launch_link(const jfof_cells &c, const FofBuffers &fb, const LinkParams &lp, int32_t *label,
                  const DevStatus &st, cudaStream_t s) {
     int64_t N = c.n;
-    ensure_sub_offsets();
+    ensure_link_tables();
     float b2 = host_mul(c.b, c.b);
     double gap = 1.02 * double(c.b);
     LinkGeom g{c.L, 0.5f * c.L, b2, float(double(c.n_axis) / double(c.L)), lp.inv_fine,

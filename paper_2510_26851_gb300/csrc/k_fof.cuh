@@ -50,6 +50,12 @@ struct LinkParams {
 };
 
 size_t fof_layout(int64_t N, int n, FofBuffers *fb, void *base);
+
+// Host-side argument rules shared by the ABI entry points (api.cu).
+bool finite_pos(float x);
+int check_box(int64_t N, float L, float b);
+int32_t max_cells(float L, float b);
+int resolve_n(int64_t N, float L, float b, int32_t n_axis, int32_t *out);
 LinkParams make_link_params(int64_t N, float L, float b, int n, int S, int T);
 void launch_bin_cells(const float *pos, int64_t N, float L, int n, bool wrap, const LinkParams &lp,
                       const FofBuffers &fb, const DevStatus &st, cudaStream_t s);
