@@ -24,6 +24,14 @@ inline int grid_for(int64_t work, int threads, int per_sm = 8) {
     return int(want < cap ? want : cap);
 }
 
+// One thread per work item (no grid-stride loop): blocks are scheduled in
+// order, so the items in flight stay a contiguous window -- better locality
+// than a persistent grid whose warps drift apart.
+inline unsigned grid_full(int64_t work, int threads) {
+    int64_t want = (work + threads - 1) / threads;
+    return unsigned(want < 1 ? 1 : want);
+}
+
 // Context-wide state passed to kernels by value.
 struct DevStatus {
     int *status;        // device word: first latched error code

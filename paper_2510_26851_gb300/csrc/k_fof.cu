@@ -259,6 +259,14 @@ __device__ __forceinline__ float4 shfl4(float4 v, int src) {
                        __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
 }
 
+// Next task of a warp from a work counter (dynamic scheduling keeps the
+// tasks in flight a contiguous window of the work list).
+__device__ __forceinline__ int64_t next_task(uint32_t *ctr, int lane) {
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(ctr, 1u);
+    return int64_t(__shfl_sync(0xffffffffu, t, 0));
+}
+
 __global__ void iota_kernel(int *__restrict__ p, int64_t N) {
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x)
         p[i] = int(i);
@@ -338,8 +346,8 @@ __global__ void __launch_bounds__(32 * kMedWarps) medium_local_kernel(const floa
                                                                       const uint32_t *__restrict__ cell_start,
                                                                       const uint32_t *__restrict__ medium_cells,
                                                                       const uint32_t *__restrict__ nmedium,
-                                                                      int64_t M_cap, LinkGeom g, int *parent,
-                                                                      DevStatus st) {
+                                                                      uint32_t *next, int64_t M_cap, LinkGeom g,
+                                                                      int *parent, DevStatus st) {
     __shared__ float4 sh_p[kMedWarps][kMedCap];
     __shared__ int sh_l[kMedWarps][kMedCap];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -347,7 +355,7 @@ __global__ void __launch_bounds__(32 * kMedWarps) medium_local_kernel(const floa
     int *lp = sh_l[w];
     int64_t M = *nmedium;
     if (M > M_cap) M = M_cap;
-    for (int64_t t = int64_t(blockIdx.x) * kMedWarps + w; t < M; t += int64_t(gridDim.x) * kMedWarps) {
+    for (int64_t t = next_task(next, lane); t < M; t = next_task(next, lane)) {
         uint32_t ga = medium_cells[t];
         uint32_t a0 = cell_start[ga];
         int mA = int(cell_start[ga + 1] - a0);
@@ -364,6 +372,39 @@ __global__ void __launch_bounds__(32 * kMedWarps) medium_local_kernel(const floa
             lp[q] = q;
         }
         __syncwarp();
+        if (mA <= 64) {
+            // Warp-synchronous components for up to 64 particles: each lane owns
+            // particles lane and lane+32 and builds their 64-bit adjacency masks
+            // (every pair tested with the exact predicate), then the reach sets
+            // are closed under r_j |= r_i for i in r_j (each round doubles the
+            // path length covered) until no mask changes.  The component's
+            // smallest local index is the lowest set bit.
+            const bool h0 = lane < mA, h1 = lane + 32 < mA;
+            float4 q0 = h0 ? sp[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 q1 = h1 ? sp[lane + 32] : make_float4(0.f, 0.f, 0.f, 0.f);
+            unsigned long long r0 = h0 ? 1ull << lane : 0ull, r1 = h1 ? 1ull << (lane + 32) : 0ull;
+            for (int i = 0; i < mA; ++i) {
+                float4 pi = sp[i];
+                if (h0 && linked(pi, q0, g)) r0 |= 1ull << i;
+                if (h1 && linked(pi, q1, g)) r1 |= 1ull << i;
+            }
+            for (int round = 0; round < 8; ++round) {
+                unsigned long long n0 = r0, n1 = r1;
+                for (int i = 0; i < mA; ++i) {
+                    unsigned long long ri = __shfl_sync(0xffffffffu, i < 32 ? r0 : r1, i & 31);
+                    if ((r0 >> i) & 1ull) n0 |= ri;
+                    if ((r1 >> i) & 1ull) n1 |= ri;
+                }
+                bool changed = n0 != r0 || n1 != r1;
+                r0 = n0;
+                r1 = n1;
+                if (!__any_sync(0xffffffffu, changed)) break;
+            }
+            if (h0) parent[a0 + lane] = int(a0) + __ffsll((long long)r0) - 1;
+            if (h1) parent[a0 + lane + 32] = int(a0) + __ffsll((long long)r1) - 1;
+            __syncwarp();
+            continue;
+        }
         for (int cb = 0; cb * 32 < mA; ++cb) {
             int j = cb * 32 + lane;
             bool has = j < mA;
@@ -387,14 +428,13 @@ __global__ void __launch_bounds__(32 * kMedWarps) medium_local_kernel(const floa
 __global__ void __launch_bounds__(256) medium_kernel(const float4 *__restrict__ spos,
                                                      const uint32_t *__restrict__ cell_start,
                                                      const uint32_t *__restrict__ medium_cells,
-                                                     const uint32_t *__restrict__ nmedium,
+                                                     const uint32_t *__restrict__ nmedium, uint32_t *next,
                                                      const uint32_t *__restrict__ dense_id, int64_t M_cap,
                                                      LinkGeom g, int *parent, DevStatus st) {
     const int lane = threadIdx.x & 31;
     int64_t M = *nmedium;
     if (M > M_cap) M = M_cap;
-    int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
-    for (int64_t t = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; t < M; t += nw) {
+    for (int64_t t = next_task(next, lane); t < M; t = next_task(next, lane)) {
         uint32_t ga = medium_cells[t];
         int cx, cy, cz;
         decode_cell(ga, g.nb, cx, cy, cz);
@@ -469,14 +509,16 @@ __device__ __forceinline__ int sub_key(float4 q, const LinkGeom &g, int cx, int 
 // when the two sub-cells are already in one component, else the pair of
 // sub-cells is tested until its first link.
 template <int O0, int R>
-__device__ __forceinline__ void dense_round(const uint16_t *ne, int nF, int k, const uint16_t *ss, int *lp,
-                                            const float4 *__restrict__ cp, const LinkGeom &g, int lane) {
+__device__ __forceinline__ void dense_round(const uint32_t *ne, int nF, int k, const uint16_t *ss, int *lp,
+                                            const float4 *__restrict__ cp, const LinkGeom &g, int lane,
+                                            const int *offs) {
     const int total = nF * R;
     for (int p = lane; p < total; p += 32) {
-        int F = ne[p / R];
-        int o = O0 + p % R;
-        int fz = F / (k * k), rem = F - fz * k * k, fy = rem / k, fx = rem - fy * k;
-        int gx = fx + c_sub62[o][0], gy = fy + c_sub62[o][1], gz = fz + c_sub62[o][2];
+        uint32_t e = ne[p / R];  // key | x << 10 | y << 14 | z << 18
+        int F = int(e & 1023u);
+        int o = offs[O0 + p % R];  // (dx+2) | (dy+2) << 3 | (dz+2) << 6
+        int gx = int((e >> 10) & 15u) + (o & 7) - 2, gy = int((e >> 14) & 15u) + ((o >> 3) & 7) - 2,
+            gz = int((e >> 18) & 15u) + ((o >> 6) & 7) - 2;
         if (unsigned(gx) >= unsigned(k) || unsigned(gy) >= unsigned(k) || unsigned(gz) >= unsigned(k)) continue;
         int G = gx + k * (gy + k * gz);
         int g0 = ss[G], g1 = ss[G + 1];
@@ -502,19 +544,23 @@ __global__ void __launch_bounds__(32 * kDenseWarps) dense_cells_kernel(float4 *_
                                                                        const uint32_t *__restrict__ cell_start,
                                                                        const uint32_t *__restrict__ dense_cells,
                                                                        const uint32_t *__restrict__ ndense,
-                                                                       uint16_t *__restrict__ sub_start,
+                                                                       uint32_t *next, uint16_t *__restrict__ sub_start,
                                                                        int *__restrict__ parent, LinkGeom g) {
     __shared__ int sh_cnt[kDenseWarps][kSubMax + 1];
     __shared__ uint16_t sh_ss[kDenseWarps][kSubMax + 2];
-    __shared__ uint16_t sh_ne[kDenseWarps][kSubMax + 1];
+    __shared__ uint32_t sh_ne[kDenseWarps][kSubMax + 1];
+    __shared__ int sh_off[62];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int *cnt = sh_cnt[w];
     uint16_t *ss = sh_ss[w];
-    uint16_t *ne = sh_ne[w];
+    uint32_t *ne = sh_ne[w];
+    for (int o = threadIdx.x; o < 62; o += blockDim.x)
+        sh_off[o] = (c_sub62[o][0] + 2) | ((c_sub62[o][1] + 2) << 3) | ((c_sub62[o][2] + 2) << 6);
+    __syncthreads();
     int64_t D = *ndense;
     if (D > g.D_cap) D = g.D_cap;
     const int k = g.k, k3 = g.k3;
-    for (int64_t d = int64_t(blockIdx.x) * kDenseWarps + w; d < D; d += int64_t(gridDim.x) * kDenseWarps) {
+    for (int64_t d = next_task(next, lane); d < D; d = next_task(next, lane)) {
         uint32_t gidx = dense_cells[d];
         uint32_t start = cell_start[gidx];
         int m = int(cell_start[gidx + 1] - start);
@@ -553,7 +599,10 @@ __global__ void __launch_bounds__(32 * kDenseWarps) dense_cells_kernel(float4 *_
             ss[key] = uint16_t(pre);
             tab[key] = uint16_t(pre);
             cnt[key] = pre;
-            if (c > 0) ne[pn++] = uint16_t(key);
+            if (c > 0) {
+                int kz = key / (k * k), ky = (key / k) % k, kx = key % k;
+                ne[pn++] = uint32_t(key) | uint32_t(kx) << 10 | uint32_t(ky) << 14 | uint32_t(kz) << 18;
+            }
             pre += c;
         }
         if (lane == 0) {
@@ -569,14 +618,18 @@ __global__ void __launch_bounds__(32 * kDenseWarps) dense_cells_kernel(float4 *_
         __syncwarp();
         for (int key = lane; key < k3; key += 32) cnt[key] = key;
         __syncwarp();
-        dense_round<0, kSubNear>(ne, nF, k, ss, cnt, spos + start, g, lane);
+        dense_round<0, kSubNear>(ne, nF, k, ss, cnt, spos + start, g, lane, sh_off);
+        __syncwarp();
+        // full compression: every sub-cell points at its root, so the finds of
+        // the second round are one load deep
+        for (int i = lane; i < nF; i += 32) cnt[ne[i] & 1023u] = lfind(cnt, int(ne[i] & 1023u));
         __syncwarp();
         // the second round (offsets with a component of +-2) can only join
         // sub-cells still in different components: skip it when one is left
         bool split = false;
-        int r0 = lfind(cnt, ne[0]);
-        for (int i = lane; i < nF; i += 32) split |= lfind(cnt, ne[i]) != r0;
-        if (__any_sync(0xffffffffu, split)) dense_round<kSubNear, 62 - kSubNear>(ne, nF, k, ss, cnt, spos + start, g, lane);
+        int r0 = lfind(cnt, int(ne[0] & 1023u));
+        for (int i = lane; i < nF; i += 32) split |= lfind(cnt, int(ne[i] & 1023u)) != r0;
+        if (__any_sync(0xffffffffu, split)) dense_round<kSubNear, 62 - kSubNear>(ne, nF, k, ss, cnt, spos + start, g, lane, sh_off);
         __syncwarp();
         for (int t = lane; t < m; t += 32) {
             float4 q = spos[start + t];
@@ -597,7 +650,7 @@ __global__ void __launch_bounds__(32 * kDenseWarps) dense_cells_kernel(float4 *_
 __global__ void __launch_bounds__(256) dense_nbr_kernel(const float4 *__restrict__ spos,
                                                         const uint32_t *__restrict__ cell_start,
                                                         const uint32_t *__restrict__ dense_cells,
-                                                        const uint32_t *__restrict__ ndense,
+                                                        const uint32_t *__restrict__ ndense, uint32_t *next,
                                                         const uint32_t *__restrict__ dense_id,
                                                         const uint16_t *__restrict__ sub_start, LinkGeom g,
                                                         int *parent, DevStatus st) {
@@ -605,8 +658,7 @@ __global__ void __launch_bounds__(256) dense_nbr_kernel(const float4 *__restrict
     int64_t D = *ndense;
     if (D > g.D_cap) D = g.D_cap;
     const int k = g.k;
-    int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
-    for (int64_t d = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; d < D; d += nw) {
+    for (int64_t d = next_task(next, lane); d < D; d = next_task(next, lane)) {
         if (g.n < 3) break;
         uint32_t ga = dense_cells[d];
         int cx, cy, cz;
@@ -794,31 +846,34 @@ void launch_link(const jfof_cells &c, const FofBuffers &fb, const LinkParams &lp
         JFOF_TRACE("link_init", s);
         iota_kernel<<<grid_for(N, 256), 256, 0, s>>>(fb.parent, N);
     }
+    cudaMemsetAsync(fb.counters + 2, 0, 4 * sizeof(uint32_t), s);  // work counters
     // local passes first: they write parent with plain stores, each for its own cell
     if (lp.T > 0) {
         JFOF_TRACE("dense_cells", s);
         dense_cells_kernel<<<grid_for(lp.D_cap * 32, 32 * kDenseWarps, 8), 32 * kDenseWarps, 0, s>>>(
-            fb.spos, fb.tmp, c.cell_start, fb.dense_cells, fb.counters, fb.sub_start, fb.parent, g);
+            fb.spos, fb.tmp, c.cell_start, fb.dense_cells, fb.counters, fb.counters + 2, fb.sub_start, fb.parent, g);
     }
     {
         JFOF_TRACE("link_medium_local", s);
         medium_local_kernel<<<grid_for(medium_cap(N) * 32, 32 * kMedWarps, 8), 32 * kMedWarps, 0, s>>>(
-            spos, c.cell_start, fb.medium_cells, fb.counters + 1, medium_cap(N), g, fb.parent, st);
+            spos, c.cell_start, fb.medium_cells, fb.counters + 1, fb.counters + 3, medium_cap(N), g, fb.parent, st);
     }
     // then everything that unites across cells (atomic hooks only)
     if (lp.S > 0) {
         JFOF_TRACE("link_small", s);
-        small_kernel<<<grid_for(N, 256), 256, 0, s>>>(spos, c.cell_start, N, g, fb.parent, st);
+        small_kernel<<<grid_full(N, 256), 256, 0, s>>>(spos, c.cell_start, N, g, fb.parent, st);
     }
     {
         JFOF_TRACE("link_medium", s);
         medium_kernel<<<grid_for(medium_cap(N) * 32, 256, 8), 256, 0, s>>>(
-            spos, c.cell_start, fb.medium_cells, fb.counters + 1, fb.dense_id, medium_cap(N), g, fb.parent, st);
+            spos, c.cell_start, fb.medium_cells, fb.counters + 1, fb.counters + 4, fb.dense_id, medium_cap(N), g,
+            fb.parent, st);
     }
     if (lp.T > 0) {
         JFOF_TRACE("link_dense_nbr", s);
         dense_nbr_kernel<<<grid_for(lp.D_cap * 32, 256, 8), 256, 0, s>>>(
-            spos, c.cell_start, fb.dense_cells, fb.counters, fb.dense_id, fb.sub_start, g, fb.parent, st);
+            spos, c.cell_start, fb.dense_cells, fb.counters, fb.counters + 5, fb.dense_id, fb.sub_start, g, fb.parent,
+            st);
     }
     int *rootmin = reinterpret_cast<int *>(fb.tmp);
     cudaMemsetAsync(rootmin, 0x7f, sizeof(int) * size_t(N), s);

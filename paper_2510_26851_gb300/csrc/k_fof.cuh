@@ -12,7 +12,7 @@ constexpr int kSubSide = 9;
 constexpr int kSubMax = kSubSide * kSubSide * kSubSide;  // 729
 constexpr uint32_t kDenseMaxM = 65535;
 constexpr int kDefaultDenseThreshold = 64;
-constexpr int kDefaultSmallThreshold = 8;
+constexpr int kDefaultSmallThreshold = 4;
 
 // One IEEE binary32 multiply on the host (b*b for the link threshold).
 inline float host_mul(float a, float b) {
@@ -35,7 +35,7 @@ struct FofBuffers {
     int *parent;           // [N]
     uint32_t *dense_id;    // [cell table]
     uint32_t *dense_cells; // [D_cap]
-    uint32_t *counters;    // [2]: dense cells, medium cells
+    uint32_t *counters;    // [6]: dense cells, medium cells, four work counters
     uint16_t *sub_start;   // [D_cap][kSubMax + 1]
     uint32_t *medium_cells;// [medium_cap]
 };

@@ -10,6 +10,7 @@
 //               halo so that every later reduction runs in a fixed order
 #include "jfof_internal.cuh"
 #include "k_fof.cuh"
+#include "k_reinforce.cuh"
 
 namespace jfof {
 
@@ -67,67 +68,6 @@ __global__ void __launch_bounds__(256) members_fill_kernel(const int32_t *__rest
     }
 }
 
-// Ascending sort of each halo's member segment.  Sorting network with only
-// ascending comparators (each merge stage starts with the "flip" comparator
-// t <-> t ^ (k-1), then t <-> t ^ j for halving j), which lets a segment of
-// any length m be treated as padded with +inf up to a power of two: a
-// comparator whose upper index is >= m never moves anything and is skipped.
-constexpr int kSegThreads = 256;
-constexpr int kSegSmem = 8192;
-
-template <class Acc>
-__device__ void sort_network(Acc a, int m) {
-    int P = 1;
-    while (P < m) P <<= 1;
-    for (int k = 2; k <= P; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int t = threadIdx.x; t < P; t += blockDim.x) {
-                int u = (j == (k >> 1)) ? (t ^ (k - 1)) : (t ^ j);
-                if (u > t && u < m) {
-                    int x = a.get(t), y = a.get(u);
-                    if (x > y) {
-                        a.set(t, y);
-                        a.set(u, x);
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-}
-
-struct SmemAcc {
-    int *p;
-    __device__ __forceinline__ int get(int i) const { return p[i]; }
-    __device__ __forceinline__ void set(int i, int v) const { p[i] = v; }
-};
-struct GlobAcc {
-    int32_t *p;
-    __device__ __forceinline__ int get(int i) const { return p[i]; }
-    __device__ __forceinline__ void set(int i, int v) const { p[i] = v; }
-};
-
-__global__ void __launch_bounds__(kSegThreads) members_sort_kernel(const int32_t *__restrict__ halo_start,
-                                                                   const int32_t *__restrict__ n_halos,
-                                                                   int32_t *__restrict__ members) {
-    __shared__ int buf[kSegSmem];
-    int H = *n_halos;
-    for (int h = blockIdx.x; h < H; h += gridDim.x) {
-        int hs = halo_start[h], m = halo_start[h + 1] - hs;
-        if (m <= 1) continue;
-        if (m <= kSegSmem) {
-            for (int t = threadIdx.x; t < m; t += blockDim.x) buf[t] = members[hs + t];
-            __syncthreads();
-            sort_network(SmemAcc{buf}, m);
-            for (int t = threadIdx.x; t < m; t += blockDim.x) members[hs + t] = buf[t];
-            __syncthreads();
-        } else {
-            // very large group: the same network in global memory (slow path)
-            sort_network(GlobAcc{members + hs}, m);
-        }
-    }
-}
-
 size_t groups_layout(int64_t N, int64_t H_cap, GroupBuffers *gb, void *base) {
     char *p = reinterpret_cast<char *>(base);
     size_t off = 0;
@@ -166,11 +106,8 @@ void launch_groups(const int32_t *label, int64_t N, int32_t min_size, int64_t H_
         JFOF_TRACE("members_fill", s);
         members_fill_kernel<<<grid_for(N, 256), 256, 0, s>>>(halo_id, N, gb.cursor, members);
     }
-    {
-        JFOF_TRACE("members_sort", s);
-        members_sort_kernel<<<grid_for(H_cap * kSegThreads, kSegThreads, 8), kSegThreads, 0, s>>>(halo_start, n_halos,
-                                                                                                 members);
-    }
+    // members of each halo ascending by original index (segments past H are empty)
+    launch_segsort(reinterpret_cast<const uint32_t *>(halo_start), H_cap, members, N, s, n_halos);
 }
 
 }  // namespace jfof

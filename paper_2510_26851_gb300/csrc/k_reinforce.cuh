@@ -6,7 +6,9 @@ namespace jfof {
 
 // Sorts data[off[t] .. off[t+1]) ascending for every t < S whose segment ends
 // within cap elements (segments past cap are left alone).
-void launch_segsort(const uint32_t *off, int64_t S, int32_t *data, int64_t cap, cudaStream_t s);
+// S_dev (optional, device): a tighter segment count read by the kernel.
+void launch_segsort(const uint32_t *off, int64_t S, int32_t *data, int64_t cap, cudaStream_t s,
+                    const int32_t *S_dev = nullptr);
 
 // Views into the pair-list workspace.
 struct PairBuffers {

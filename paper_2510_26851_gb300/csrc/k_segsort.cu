@@ -40,7 +40,9 @@ struct PtrAcc {
 };
 
 __global__ void __launch_bounds__(32 * kSegWarps) segsort_kernel(const uint32_t *__restrict__ off, int64_t S,
-                                                                 int64_t cap, int32_t *__restrict__ data) {
+                                                                 const int32_t *__restrict__ S_dev, int64_t cap,
+                                                                 int32_t *__restrict__ data) {
+    if (S_dev && int64_t(*S_dev) < S) S = *S_dev;
     __shared__ int buf[kSegWarps][kSegWarpSmem];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int64_t sgi = int64_t(blockIdx.x) * kSegWarps + w; sgi < S; sgi += int64_t(gridDim.x) * kSegWarps) {
@@ -70,9 +72,10 @@ __global__ void __launch_bounds__(32 * kSegWarps) segsort_kernel(const uint32_t 
     }
 }
 
-void launch_segsort(const uint32_t *off, int64_t S, int32_t *data, int64_t cap, cudaStream_t s) {
+void launch_segsort(const uint32_t *off, int64_t S, int32_t *data, int64_t cap, cudaStream_t s,
+                    const int32_t *S_dev) {
     JFOF_TRACE("segsort", s);
-    segsort_kernel<<<grid_for(S * 32, 32 * kSegWarps, 8), 32 * kSegWarps, 0, s>>>(off, S, cap, data);
+    segsort_kernel<<<grid_for(S * 32, 32 * kSegWarps, 8), 32 * kSegWarps, 0, s>>>(off, S, S_dev, cap, data);
 }
 
 }  // namespace jfof

@@ -94,5 +94,5 @@ def test_autotuner_choice_keeps_labels(J):
         r = J.fof(pos, spec.L, spec.b, spec.min_size, n_axis=n)
         J.sync()
     finally:
-        J.set_cell_classes(8, 64)
+        J.set_cell_classes()
     assert np.array_equal(r.label.cpu().numpy(), ref)

@@ -100,7 +100,7 @@ def test_labels_invariant_across_cell_classes(J, boost):
             _, r, H = run_fof(J, pos_np, spec.L, spec.b, spec.min_size)
             assert np.array_equal(r.label.cpu().numpy(), lab_ref), (S, T)
     finally:
-        J.set_cell_classes(8, 64)
+        J.set_cell_classes()
 
 
 def test_ragged_sizes_and_tiny_boxes(J):
