@@ -307,6 +307,29 @@ int jfof_fof(jfof_ctx *ctx, const float *pos, int64_t N, float L, float b, int32
              int32_t *halo_id, int32_t *count, int32_t *halo_start, int32_t *members,
              int32_t *n_halos);
 
+/* ---------------------------------------------------------------------- */
+/* No-allocation variant (the paper has no counterpart).                   */
+
+/* jfof_fof without a workspace argument, for callers that must not allocate
+   device memory: e.g. an in-situ analysis hook inside a simulation or
+   framework that owns all device memory through its own pool, or a
+   latency-critical path that cannot afford the implicit device-wide
+   synchronisation cudaMalloc/cudaFree may perform.  Inputs and outputs are
+   the caller's, exactly as for jfof_fof (same results).  The scratch is a
+   fixed 16 MiB device array inside the library, present on every GPU that
+   loads it until the process exits; the call allocates nothing.
+   Limit: jfof_fof_all_bytes(N, n_axis) must not exceed 16 MiB (about
+   1.3e5 particles at the default grid); larger inputs return JFOF_ENOMEM
+   before any work is enqueued.
+   The first call on a device looks up the array's device address with that
+   device current (a synchronous runtime call); make that first call before
+   any stream capture.  All calls share the one array: calls whose work
+   overlaps on the same GPU race on it, so the caller must serialise them
+   (one stream, or events).  Each call initialises all the scratch it reads. */
+int jfof_fof_static(jfof_ctx *ctx, const float *pos, int64_t N, float L, float b, int32_t n_axis,
+                    uint32_t flags, int32_t min_size, int32_t *label, int32_t *halo_id,
+                    int32_t *count, int32_t *halo_start, int32_t *members, int32_t *n_halos);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,6 +31,7 @@ EXPORTED = [
     "jfof_prob_coef", "jfof_pairs_bytes", "jfof_pairs", "jfof_reinforce_sample_bytes",
     "jfof_reinforce_sample", "jfof_reinforce_grad_bytes", "jfof_reinforce_grad", "jfof_eval_exp",
     "jfof_eval_edge_uniform", "jfof_batch_bytes", "jfof_fof_batched", "jfof_autotune",
+    "jfof_fof_static",
 ]
 
 
@@ -93,6 +94,7 @@ def _declare(lib):
         "jfof_fof_batched": [vp, vp, vp, i32, vp, vp, vp, vp, vp, u32, i32, vp, sz, vp, vp, vp, i32],
         "jfof_autotune": [vp, vp, i64, f32, f32, u32, i32, vp, sz, vp, vp, vp, i32, P(i32), P(i32),
                           P(i32), P(f32)],
+        "jfof_fof_static": [vp, vp, i64, f32, f32, i32, u32, i32, vp, vp, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -596,3 +598,24 @@ def autotune(pos: torch.Tensor, L: float, b: float, min_size: int = 20, reps: in
                                    ctypes.byref(bn), ctypes.byref(bs), ctypes.byref(bd), ctypes.byref(ms)),
            "jfof_autotune")
     return bn.value, bs.value, bd.value, ms.value
+
+
+def fof_static(pos: torch.Tensor, L: float, b: float, min_size: int = 20, n_axis: int = 0,
+               wrap: bool = False, out: FofResult | None = None) -> FofResult:
+    """a1-a7 like :func:`fof`, with the library's fixed 16 MiB device scratch
+    instead of a workspace (for callers that must not allocate device memory;
+    about 1.3e5 particles at most).  Calls sharing a GPU must not overlap."""
+    _need(pos, torch.float32, None, "pos")
+    N = pos.shape[0]
+    dev = pos.device
+    n = default_cells_per_axis(N, L, b) if n_axis == 0 else int(n_axis)
+    if out is not None:
+        label, g = out.label, out.groups
+    else:
+        label = torch.empty(N, dtype=torch.int32, device=dev)
+        g = _alloc_groups(N, min_size, dev)
+    _check(library().jfof_fof_static(context(dev), _ptr(pos), N, L, b, n, JFOF_WRAP if wrap else 0,
+                                     min_size, _ptr(label), _ptr(g.halo_id), _ptr(g.count),
+                                     _ptr(g.halo_start), _ptr(g.members), _ptr(g.n_halos_dev)),
+           "jfof_fof_static")
+    return FofResult(label, g, n)
