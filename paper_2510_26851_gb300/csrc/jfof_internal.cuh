@@ -137,6 +137,27 @@ __device__ __forceinline__ void uf_unite(int *parent, int a, int b, const DevSta
     latch(st, JFOF_ETIMEOUT);
 }
 
+// uf_unite that also returns a member of the merged component (the root it
+// hooked under), for callers that cache component representatives.
+__device__ __forceinline__ int uf_unite_rep(int *parent, int a, int b, const DevStatus &st) {
+    int ra = uf_find(parent, a);
+    int rb = uf_find(parent, b);
+    for (int64_t it = 0; it < st.loop_budget; ++it) {
+        if (ra == rb) return ra;
+        if (ra < rb) {
+            int t = ra;
+            ra = rb;
+            rb = t;
+        }
+        int old = atomicCAS(&parent[ra], ra, rb);
+        if (old == ra) return rb;
+        ra = uf_find(parent, old);
+        rb = uf_find(parent, rb);
+    }
+    latch(st, JFOF_ETIMEOUT);
+    return rb;
+}
+
 // ---------------------------------------------------------------------------
 // Device-wide exclusive scan of uint32 values produced by a functor
 // op(i) for i in [0, n): out[i] = sum_{k<i} op(k), out[n] = total.

@@ -450,6 +450,13 @@ __global__ void __launch_bounds__(256) medium_kernel(const float4 *__restrict__ 
             nb1 = cell_start[gb + 1];
             ncls = cell_class(nb1 - nb0, gb, g, dense_id);
         }
+        // Cached component representatives of the cell's first 64 particles
+        // (lane holds particles lane and lane+32).  Equal representatives
+        // mean one component, so such a linked pair needs no union; after a
+        // union every cached value naming either side becomes the merged
+        // representative.  A stale value only costs an exact union.
+        int rep0 = lane < mA ? uf_find(parent, int(a0 + lane)) : -1;
+        int rep1 = lane + 32 < mA ? uf_find(parent, int(a0 + lane + 32)) : -1;
         for (int o = 0; o < 26; ++o) {
             int cls = __shfl_sync(0xffffffffu, ncls, o);
             if (cls == 0 || cls == 3 || (cls == 2 && o >= 13)) continue;
@@ -476,12 +483,26 @@ __global__ void __launch_bounds__(256) medium_kernel(const float4 *__restrict__ 
                         inb = gap_to_neighbour(qb, bx, by, bz, -ox, -oy, -oz, g.cell_side) <= g.gap2;
                     }
                     if (!__ballot_sync(0xffffffffu, inb)) continue;
+                    int repb = inb ? uf_find(parent, int(b0 + j)) : -2;
                     unsigned bits = ma;
                     while (bits) {
                         int src = __ffs(bits) - 1;
                         bits &= bits - 1;
                         float4 x = shfl4(pa, src);
-                        if (inb && linked(x, qb, g)) uf_unite(parent, int(a0 + ca + src), int(b0 + j), st);
+                        int ra = ca == 0 ? __shfl_sync(0xffffffffu, rep0, src)
+                                         : (ca == 32 ? __shfl_sync(0xffffffffu, rep1, src) : -3);
+                        bool join = inb && ra != repb && linked(x, qb, g);
+                        int merged = join ? uf_unite_rep(parent, int(a0 + ca + src), int(b0 + j), st) : 0;
+                        unsigned um = __ballot_sync(0xffffffffu, join);
+                        while (um) {
+                            int L = __ffs(um) - 1;
+                            um &= um - 1;
+                            int s1 = __shfl_sync(0xffffffffu, ra, L), s2 = __shfl_sync(0xffffffffu, repb, L);
+                            int nr = __shfl_sync(0xffffffffu, merged, L);
+                            if (rep0 == s1 || rep0 == s2) rep0 = nr;
+                            if (rep1 == s1 || rep1 == s2) rep1 = nr;
+                            if (repb == s1 || repb == s2) repb = nr;
+                        }
                     }
                 }
             }
