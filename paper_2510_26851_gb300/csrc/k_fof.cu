@@ -372,6 +372,27 @@ __global__ void __launch_bounds__(32 * kMedWarps) medium_local_kernel(const floa
             lp[q] = q;
         }
         __syncwarp();
+        if (mA <= 32) {
+            // one particle per lane: 32-bit adjacency masks, same closure
+            const bool h0 = lane < mA;
+            float4 q0 = h0 ? sp[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+            unsigned r0 = h0 ? 1u << lane : 0u;
+            for (int i = 0; i < mA; ++i)
+                if (h0 && linked(sp[i], q0, g)) r0 |= 1u << i;
+            for (int round = 0; round < 6; ++round) {
+                unsigned n0 = r0;
+                for (int i = 0; i < mA; ++i) {
+                    unsigned ri = __shfl_sync(0xffffffffu, r0, i);
+                    if ((r0 >> i) & 1u) n0 |= ri;
+                }
+                bool changed = n0 != r0;
+                r0 = n0;
+                if (!__any_sync(0xffffffffu, changed)) break;
+            }
+            if (h0) parent[a0 + lane] = int(a0) + __ffs(int(r0)) - 1;
+            __syncwarp();
+            continue;
+        }
         if (mA <= 64) {
             // Warp-synchronous components for up to 64 particles: each lane owns
             // particles lane and lane+32 and builds their 64-bit adjacency masks
@@ -571,12 +592,20 @@ __global__ void __launch_bounds__(32 * kDenseWarps) dense_cells_kernel(float4 *_
     __shared__ uint16_t sh_ss[kDenseWarps][kSubMax + 2];
     __shared__ uint32_t sh_ne[kDenseWarps][kSubMax + 1];
     __shared__ int sh_off[62];
+    __shared__ int sh_off2[2 * (62 - kSubNear)];
+    __shared__ int sh_sz[kDenseWarps][kSubMax + 1];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int *cnt = sh_cnt[w];
     uint16_t *ss = sh_ss[w];
     uint32_t *ne = sh_ne[w];
+    int *sz = sh_sz[w];
     for (int o = threadIdx.x; o < 62; o += blockDim.x)
         sh_off[o] = (c_sub62[o][0] + 2) | ((c_sub62[o][1] + 2) << 3) | ((c_sub62[o][2] + 2) << 6);
+    for (int o = threadIdx.x; o < 62 - kSubNear; o += blockDim.x) {
+        int dx = c_sub62[kSubNear + o][0], dy = c_sub62[kSubNear + o][1], dz = c_sub62[kSubNear + o][2];
+        sh_off2[2 * o] = (dx + 2) | ((dy + 2) << 3) | ((dz + 2) << 6);
+        sh_off2[2 * o + 1] = (2 - dx) | ((2 - dy) << 3) | ((2 - dz) << 6);
+    }
     __syncthreads();
     int64_t D = *ndense;
     if (D > g.D_cap) D = g.D_cap;
@@ -645,12 +674,43 @@ __global__ void __launch_bounds__(32 * kDenseWarps) dense_cells_kernel(float4 *_
         // the second round are one load deep
         for (int i = lane; i < nF; i += 32) cnt[ne[i] & 1023u] = lfind(cnt, int(ne[i] & 1023u));
         __syncwarp();
-        // the second round (offsets with a component of +-2) can only join
-        // sub-cells still in different components: skip it when one is left
-        bool split = false;
-        int r0 = lfind(cnt, int(ne[0] & 1023u));
-        for (int i = lane; i < nF; i += 32) split |= lfind(cnt, int(ne[i] & 1023u)) != r0;
-        if (__any_sync(0xffffffffu, split)) dense_round<kSubNear, 62 - kSubNear>(ne, nF, k, ss, cnt, spos + start, g, lane, sh_off);
+        // The second round (offsets with a component of +-2) can only join
+        // sub-cells still in different components.  Every such pair has an end
+        // outside the largest component, so the round runs only from the
+        // sub-cells outside it, over the far offsets in both directions.
+        for (int key = lane; key < k3; key += 32) sz[key] = 0;
+        __syncwarp();
+        for (int i = lane; i < nF; i += 32) atomicAdd(&sz[cnt[ne[i] & 1023u]], 1);
+        __syncwarp();
+        int best_c = -1, best_r = -1;
+        for (int i = lane; i < nF; i += 32) {
+            int F = int(ne[i] & 1023u);
+            if (cnt[F] == F && (sz[F] > best_c || (sz[F] == best_c && F < best_r))) {
+                best_c = sz[F];
+                best_r = F;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            int oc = __shfl_xor_sync(0xffffffffu, best_c, o), orr = __shfl_xor_sync(0xffffffffu, best_r, o);
+            if (oc > best_c || (oc == best_c && orr < best_r)) {
+                best_c = oc;
+                best_r = orr;
+            }
+        }
+        __syncwarp();
+        uint32_t *minority = reinterpret_cast<uint32_t *>(sz);
+        int nmin = 0;
+        for (int base = 0; base < nF; base += 32) {
+            int i = base + lane;
+            bool out = i < nF && cnt[ne[i] & 1023u] != best_r;
+            uint32_t e = i < nF ? ne[i] : 0u;
+            unsigned mask = __ballot_sync(0xffffffffu, out);
+            __syncwarp();
+            if (out) minority[nmin + __popc(mask & ((1u << lane) - 1u))] = e;
+            nmin += __popc(mask);
+        }
+        __syncwarp();
+        if (nmin > 0) dense_round<0, 2 * (62 - kSubNear)>(minority, nmin, k, ss, cnt, spos + start, g, lane, sh_off2);
         __syncwarp();
         for (int t = lane; t < m; t += 32) {
             float4 q = spos[start + t];
