@@ -68,6 +68,8 @@ struct GroupBuffers {
     uint32_t *hid;   // [N+1]
     uint32_t *cursor;// [H_cap+1]
     uint32_t *scan_tmp;
+    uint32_t *seglist;  // segmented-sort list of long halos
+    int64_t seglist_words;
 };
 size_t groups_layout(int64_t N, int64_t H_cap, GroupBuffers *gb, void *base);
 void launch_groups(const int32_t *label, int64_t N, int32_t min_size, int64_t H_cap, const GroupBuffers &gb,

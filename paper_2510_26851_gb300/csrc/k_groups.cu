@@ -82,6 +82,8 @@ size_t groups_layout(int64_t N, int64_t H_cap, GroupBuffers *gb, void *base) {
     g.cursor = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * size_t(H_cap + 1)));
     int64_t big = N > H_cap ? N : H_cap;
     g.scan_tmp = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * scan_tmp_words(big)));
+    g.seglist_words = segsort_list_words(N);
+    g.seglist = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * size_t(g.seglist_words)));
     if (gb) *gb = g;
     return off;
 }
@@ -107,7 +109,8 @@ void launch_groups(const int32_t *label, int64_t N, int32_t min_size, int64_t H_
         members_fill_kernel<<<grid_for(N, 256), 256, 0, s>>>(halo_id, N, gb.cursor, members);
     }
     // members of each halo ascending by original index (segments past H are empty)
-    launch_segsort(reinterpret_cast<const uint32_t *>(halo_start), H_cap, members, N, s, n_halos);
+    launch_segsort(reinterpret_cast<const uint32_t *>(halo_start), H_cap, members, N, s, n_halos, gb.seglist,
+                   gb.seglist_words);
 }
 
 }  // namespace jfof

@@ -49,7 +49,14 @@ __device__ __forceinline__ float load_coord(const float *pos, int64_t i, int a, 
     return wrap ? wrap_coord(x, L) : x;
 }
 
-// One warp per halo (grid-stride over halos).
+// One warp per halo (grid-stride over halos), one gather pass over the
+// members.  Positions are summed as minimum-image offsets from the halo's
+// first member xr (periodic centre of mass); velocities as offsets from that
+// member's velocity vr, with the squares of those offsets summed alongside,
+// so the dispersion needs no second pass:
+//   vmean = vr + S1/m,  sigma^2 = (S2/m - |S1/m|^2) / 3,
+// S1 = sum(v - vr), S2 = sum |v - vr|^2 (compensated).  vr is a member, so
+// |S1/m| is of the order of sigma and the subtraction loses O(1) bits.
 __global__ void __launch_bounds__(256) halo_props_kernel(const float *__restrict__ pos, const float *__restrict__ vel,
                                                          float L, bool wrap, const int32_t *__restrict__ halo_start,
                                                          const int32_t *__restrict__ members,
@@ -66,42 +73,64 @@ __global__ void __launch_bounds__(256) halo_props_kernel(const float *__restrict
         int m = he - hs;
         float fm = float(m);
         int r = members[hs];  // smallest member: the segment is sorted
-        float xr[3];
+        float xr[3], vr[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-        for (int a = 0; a < 3; ++a) xr[a] = load_coord(pos, r, a, L, wrap);
+        for (int a = 0; a < 3; ++a) {
+            xr[a] = load_coord(pos, r, a, L, wrap);
+            if (vel) vr[a] = vel[3 * int64_t(r) + a];
+        }
         KSum sx[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         KSum sv[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-        for (int k = hs + lane; k < he; k += 32) {
-            int i = members[k];
+        KSum s2 = {0.f, 0.f};
+        for (int k0 = hs + lane; k0 < he; k0 += 64) {
+            // two members per lane per step: all six gathers issue before the sums
+            int k1 = k0 + 32;
+            bool two = k1 < he;
+            int i0 = members[k0];
+            int i1 = two ? members[k1] : i0;
+            float p0[3], p1[3], v0[3] = {0.f, 0.f, 0.f}, v1[3] = {0.f, 0.f, 0.f};
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                kadd(sx[a], min_image(load_coord(pos, i, a, L, wrap), xr[a], L, hL));
-                if (vel) kadd(sv[a], vel[3 * int64_t(i) + a]);
+                p0[a] = load_coord(pos, i0, a, L, wrap);
+                p1[a] = load_coord(pos, i1, a, L, wrap);
+                if (vel) {
+                    v0[a] = vel[3 * int64_t(i0) + a];
+                    v1[a] = vel[3 * int64_t(i1) + a];
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                if (t == 1 && !two) break;
+                const float *p = t ? p1 : p0;
+                const float *v = t ? v1 : v0;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    kadd(sx[a], min_image(p[a], xr[a], L, hL));
+                    if (vel) {
+                        float d = __fsub_rn(v[a], vr[a]);
+                        kadd(sv[a], d);
+                        kadd(s2, __fmul_rn(d, d));
+                    }
+                }
             }
         }
-        float vm[3];
+        float dm[3];
+        float dd = 0.f;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             float d = __fdiv_rn(kval(kwarp(sx[a])), fm);
             float c = wrap_coord(__fadd_rn(xr[a], d), L);
             if (lane == 0) com[3 * h + a] = c;
-            vm[a] = vel ? __fdiv_rn(kval(kwarp(sv[a])), fm) : 0.f;
+            dm[a] = vel ? __fdiv_rn(kval(kwarp(sv[a])), fm) : 0.f;
+            dd = __fadd_rn(dd, __fmul_rn(dm[a], dm[a]));
         }
         if (lane == 0) mass[h] = __fmul_rn(particle_mass, fm);
         if (!vel) continue;
-        KSum s2 = {0.f, 0.f};
-        for (int k = hs + lane; k < he; k += 32) {
-            int i = members[k];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                float d = __fsub_rn(vel[3 * int64_t(i) + a], vm[a]);
-                kadd(s2, __fmul_rn(d, d));
-            }
-        }
-        float var = __fdiv_rn(kval(kwarp(s2)), __fmul_rn(3.0f, fm));
+        float q = __fdiv_rn(kval(kwarp(s2)), fm);
+        float var = fmaxf(__fdiv_rn(__fsub_rn(q, dd), 3.0f), 0.f);
         if (lane == 0) {
 #pragma unroll
-            for (int a = 0; a < 3; ++a) vmean[3 * h + a] = vm[a];
+            for (int a = 0; a < 3; ++a) vmean[3 * h + a] = __fadd_rn(vr[a], dm[a]);
             sigv[h] = __fsqrt_rn(var);
         }
     }

@@ -175,6 +175,8 @@ size_t pairs_layout(int64_t N, int n, PairBuffers *pb, void *base) {
     b.off = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * size_t(N + 1)));
     b.scan_tmp = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * scan_tmp_words(N)));
     b.total = reinterpret_cast<unsigned long long *>(take(sizeof(unsigned long long)));
+    b.seglist_words = segsort_list_words(N);
+    b.seglist = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * size_t(b.seglist_words)));
     b.cells_ws = take(fof_layout(N, n, nullptr, nullptr));
     if (pb) *pb = b;
     return off;
@@ -206,7 +208,7 @@ void launch_pairs(const float *pos, int64_t N, const PairGeom &pg, const PairBuf
                                                           pair_i, pair_j, pb.total);
     }
     // every segment holds pairs (i, j) of one i: sort j ascending (pair_i is constant there)
-    launch_segsort(pb.off, N, pair_j, cap, s);
+    launch_segsort(pb.off, N, pair_j, cap, s, nullptr, pb.seglist, pb.seglist_words);
     {
         JFOF_TRACE("pair_props", s);
         pair_props_kernel<<<grid_for(N * 16, 256), 256, 0, s>>>(pos, pg, pb.off, N, cap, pair_i, pair_j, pair_d,
@@ -430,6 +432,8 @@ size_t grad_layout(int64_t N, int64_t E, GradBuffers *gb, void *base) {
     g.rev = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * size_t(Ee)));
     g.sumA = reinterpret_cast<float *>(take(sizeof(float)));
     g.scan_tmp = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * scan_tmp_words(N)));
+    g.seglist_words = segsort_list_words(Ee > N ? Ee : N);
+    g.seglist = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * size_t(g.seglist_words)));
     if (gb) *gb = g;
     return off;
 }
@@ -454,7 +458,7 @@ void launch_reinforce_grad(const float *pos, int64_t N, float L, bool wrap, cons
     if (E > 0) {
         cudaMemcpyAsync(gb.cursor, gb.roff, sizeof(uint32_t) * size_t(N), cudaMemcpyDeviceToDevice, s);
         reverse_fill_kernel<<<grid_for(E, 256), 256, 0, s>>>(pair_j, E, gb.cursor, gb.rev);
-        launch_segsort(gb.roff, N, gb.rev, E, s);
+        launch_segsort(gb.roff, N, gb.rev, E, s, nullptr, gb.seglist, gb.seglist_words);
     }
     {
         JFOF_TRACE("grad_gather", s);

@@ -6,9 +6,13 @@ namespace jfof {
 
 // Sorts data[off[t] .. off[t+1]) ascending for every t < S whose segment ends
 // within cap elements (segments past cap are left alone).
-// S_dev (optional, device): a tighter segment count read by the kernel.
-void launch_segsort(const uint32_t *off, int64_t S, int32_t *data, int64_t cap, cudaStream_t s,
-                    const int32_t *S_dev = nullptr);
+// S_dev (may be null, device): a tighter segment count read by the kernel.
+// list: device scratch of list_words uint32 for the segments longer than
+// 1024; segsort_list_words(cap) words hold all of them, fewer only slow the
+// overflow down.
+int64_t segsort_list_words(int64_t cap);
+void launch_segsort(const uint32_t *off, int64_t S, int32_t *data, int64_t cap, cudaStream_t s, const int32_t *S_dev,
+                    uint32_t *list, int64_t list_words);
 
 // Views into the pair-list workspace.
 struct PairBuffers {
@@ -16,6 +20,8 @@ struct PairBuffers {
     uint32_t *off;   // [N+1] exclusive scan of cnt
     uint32_t *scan_tmp;
     unsigned long long *total;  // [1] 64-bit pair count
+    uint32_t *seglist;          // segmented-sort list (bounded: overflow sorts in place)
+    int64_t seglist_words;
     void *cells_ws;  // binning workspace (fof_layout at the pair-cut grid)
 };
 size_t pairs_layout(int64_t N, int n, PairBuffers *pb, void *base);
@@ -47,6 +53,8 @@ struct GradBuffers {
     int32_t *rev;      // [E]
     float *sumA;       // [1]
     uint32_t *scan_tmp;
+    uint32_t *seglist;  // segmented-sort list (bounded: overflow sorts in place)
+    int64_t seglist_words;
 };
 size_t grad_layout(int64_t N, int64_t E, GradBuffers *gb, void *base);
 void launch_reinforce_grad(const float *pos, int64_t N, float L, bool wrap, const int32_t *pair_i,

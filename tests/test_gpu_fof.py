@@ -130,6 +130,28 @@ def test_lattice_closed_forms(J):
     assert np.array_equal(r.label.cpu().numpy(), np.arange(m ** 3)) and H == m ** 3
 
 
+def test_member_segments_of_every_length(J):
+    # fully linked clumps (side 0.2 < b / sqrt(3)) far apart, with sizes on
+    # both sides of every boundary of the segmented sort: one warp in
+    # registers up to 1024, one block in shared memory up to 8192, chunks
+    # beyond; input order shuffled so each halo's members arrive unsorted
+    rng = np.random.default_rng(7)
+    sizes = [1, 2, 3, 31, 32, 33, 64, 65, 128, 129, 255, 257, 511, 513, 1000, 1024, 1025, 2047, 2049,
+             4096, 8192, 8193, 12000]
+    L, b = 100.0, 0.5
+    pts = []
+    for t, n in enumerate(sizes):
+        c = np.array([5.0 + 9.0 * (t % 10), 5.0 + 9.0 * ((t // 10) % 10), 50.0])
+        pts.append(c + rng.uniform(0.0, 0.2, (n, 3)))
+    pos_np = np.concatenate(pts).astype(np.float32)
+    pos_np = pos_np[rng.permutation(len(pos_np))]
+    lab_ref = oracle.fof_labels(pos_np, L, b)
+    _, r, H = run_fof(J, pos_np, L, b, 1)
+    assert np.array_equal(r.label.cpu().numpy(), lab_ref)
+    check_groups(r, H, lab_ref, 1)
+    assert H == len(sizes)
+
+
 def test_wrap_flag_and_boundary(J):
     rng = np.random.default_rng(4)
     N, L, b = 30000, 12.0, 0.25

@@ -103,6 +103,37 @@ def test_gradient_matches_fp64_oracle(J, form):
     assert np.linalg.norm(ref) > 0 and err <= GRAD_RTOL, err
 
 
+def test_dense_clump_pairs_and_gradient(J):
+    # 2500 particles in a cube of side 0.8 b: every pair of the clump is a
+    # candidate, so the per-i pair lists and the reverse adjacency hold
+    # segments of every length up to 2499 (warp and block sorts alike)
+    rng = np.random.default_rng(9)
+    L = 30.0
+    b = float(np.float32(0.3))
+    clump = 15.0 + rng.uniform(0.0, 0.8 * b, (2500, 3))
+    bg = rng.uniform(0.0, L, (8000, 3))
+    pos_np = np.concatenate([clump, bg]).astype(np.float32)
+    pos_np = pos_np[rng.permutation(len(pos_np))]
+    pos = torch.from_numpy(pos_np).cuda()
+    coef = J.prob_coef(b, 0)
+    pr = J.pairs(pos, L, b, r_cut_of(b), prob_form=0, coef=coef)
+    J.sync()
+    pi, pj, pd, pp = oracle.pairs(pos_np, L, b, r_cut_of(b), 0, coef)
+    assert pr.E == len(pi) and pr.E > 2500 * 2499 // 2
+    assert np.array_equal(pr.i.cpu().numpy(), pi) and np.array_equal(pr.j.cpu().numpy(), pj)
+    assert np.array_equal(pr.p.cpu().numpy().view(np.uint32), pp.view(np.uint32))
+    K, seed = 8, 3
+    _, nh = J.reinforce_sample(pr, K, seed, 5)
+    Ls = nh.float()
+    adv = (Ls - Ls.mean() + torch.arange(K, device="cuda", dtype=torch.float32) * 0.1).contiguous()
+    g = J.reinforce_grad(pos, pr, K, seed, adv)
+    J.sync()
+    ref = oracle.reinforce_grad(pos_np, L, pi, pj, pp, K, seed, adv.cpu().numpy().astype(np.float64), 0, coef)
+    got = g.cpu().numpy().astype(np.float64)
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert np.linalg.norm(ref) > 0 and err <= GRAD_RTOL, err
+
+
 def test_autograd_function(J):
     spec, pos = small_box(N=20_000, L=42.0, seed=5)
     pr = J.pairs(pos, spec.L, spec.b)
