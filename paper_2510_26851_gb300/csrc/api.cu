@@ -81,6 +81,7 @@ size_t fof_layout(int64_t N, int n, FofBuffers *fb, void *base) {
     f.counters = reinterpret_cast<uint32_t *>(take(6 * sizeof(uint32_t)));
     f.sub_start = reinterpret_cast<uint16_t *>(take(sizeof(uint16_t) * size_t(D_cap) * (kSubMax + 1)));
     f.medium_cells = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * size_t(medium_cap(N))));
+    f.bucket_fill = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * kTailBuckets));
     if (fb) *fb = f;
     return off;
 }
@@ -304,7 +305,8 @@ int jfof_fof_all_bytes(int64_t N, int32_t n_axis, size_t *bytes) {
 int jfof_fof(jfof_ctx *ctx, const float *pos, int64_t N, float L, float b, int32_t n_axis, uint32_t flags,
              int32_t min_size, void *ws, size_t ws_bytes, int32_t *label, int32_t *halo_id, int32_t *count,
              int32_t *halo_start, int32_t *members, int32_t *n_halos) {
-    if (!ctx || !ws) return JFOF_EINVAL;
+    if (!ctx || !ws || !label || !halo_id || !count || !halo_start || !members || !n_halos || min_size < 1)
+        return JFOF_EINVAL;
     int e = check_box(N, L, b);
     if (e) return e;
     int32_t n;
@@ -315,9 +317,20 @@ int jfof_fof(jfof_ctx *ctx, const float *pos, int64_t N, float L, float b, int32
     if (ws_bytes < a + g) return JFOF_ENOMEM;
     jfof_cells cells;
     if ((e = jfof_bin_cells(ctx, pos, N, L, b, n, flags, ws, a, &cells))) return e;
-    if ((e = jfof_link(ctx, &cells, label))) return e;
-    return jfof_groups(ctx, label, N, min_size, reinterpret_cast<char *>(ws) + a, g, halo_id, count, halo_start,
-                       members, n_halos);
+    // link, then labels and groups straight from the forest
+    int64_t H_cap = N / min_size;
+    if (H_cap < 1) H_cap = 1;
+    FofBuffers fb;
+    fof_layout(N, n, &fb, ws);
+    GroupBuffers gb;
+    groups_layout(N, H_cap, &gb, reinterpret_cast<char *>(ws) + a);
+    LinkParams lp = make_link_params(N, L, b, n, cells.small_threshold, cells.dense_threshold);
+    cudaSetDevice(ctx->device);
+    CtxScope scope(ctx);
+    launch_link_core(cells, fb, lp, ctx->dev(), ctx->stream);
+    launch_tail_groups(fb, N, min_size, H_cap, gb, label, halo_id, count, halo_start, members, n_halos,
+                       ctx->stream);
+    return launch_status();
 }
 
 }  // extern "C"

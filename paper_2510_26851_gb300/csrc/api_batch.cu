@@ -58,12 +58,12 @@ static void run_box(const BoxPlan &p, const float *pos, uint32_t flags, int min_
     c.cell_start = fb.cell_start;
     c.n_cells_table = cell_table_entries(p.n);
     c.workspace = ws;
-    launch_link(c, fb, p.lp, label, st, s);
+    launch_link_core(c, fb, p.lp, st, s);
     GroupBuffers gb;
     groups_layout(p.N, p.H_cap, &gb, ws + p.fof_bytes);
-    launch_groups(label, p.N, min_size, p.H_cap, gb, halo_id, reinterpret_cast<int32_t *>(ws + p.count_off),
-                  reinterpret_cast<int32_t *>(ws + p.start_off), reinterpret_cast<int32_t *>(ws + p.members_off),
-                  n_halos, st, s);
+    launch_tail_groups(fb, p.N, min_size, p.H_cap, gb, label, halo_id, reinterpret_cast<int32_t *>(ws + p.count_off),
+                       reinterpret_cast<int32_t *>(ws + p.start_off), reinterpret_cast<int32_t *>(ws + p.members_off),
+                       n_halos, s);
 }
 
 // Cached graph of the last batch configuration.

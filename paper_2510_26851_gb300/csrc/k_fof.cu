@@ -847,28 +847,6 @@ __global__ void __launch_bounds__(256) dense_nbr_kernel(const float4 *__restrict
     }
 }
 
-// a6: raw labels.  Pass 1 freezes every slot onto its root (read-only finds,
-// so the only write to parent[s] is the root) and takes the smallest original
-// index per root; pass 2 writes label[orig] in original order.
-__global__ void __launch_bounds__(256) finalize_roots_kernel(const float4 *__restrict__ spos, int64_t N, int *parent,
-                                                             int *__restrict__ rootmin) {
-    for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < N; s += int64_t(gridDim.x) * blockDim.x) {
-        int r = uf_find_ro(parent, int(s));
-        parent[s] = r;
-        atomicMin(&rootmin[r], __float_as_int(spos[s].w));
-    }
-}
-
-__global__ void __launch_bounds__(256) finalize_labels_kernel(const float4 *__restrict__ spos, int64_t N,
-                                                              const int *__restrict__ parent,
-                                                              const int *__restrict__ rootmin,
-                                                              int32_t *__restrict__ label) {
-    for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < N; s += int64_t(gridDim.x) * blockDim.x) {
-        int orig = __float_as_int(spos[s].w);
-        label[orig] = rootmin[parent[s]];
-    }
-}
-
 // ---------------------------------------------------------------------------
 static bool g_sub62_ready[64] = {};
 
@@ -913,8 +891,8 @@ LinkParams make_link_params(int64_t N, float L, float b, int n, int S, int T) {
     return lp;
 }
 
-void launch_link(const jfof_cells &c, const FofBuffers &fb, const LinkParams &lp, int32_t *label,
-                 const DevStatus &st, cudaStream_t s) {
+void launch_link_core(const jfof_cells &c, const FofBuffers &fb, const LinkParams &lp, const DevStatus &st,
+                      cudaStream_t s) {
     int64_t N = c.n;
     ensure_link_tables();
     float b2 = host_mul(c.b, c.b);
@@ -956,16 +934,12 @@ void launch_link(const jfof_cells &c, const FofBuffers &fb, const LinkParams &lp
             spos, c.cell_start, fb.dense_cells, fb.counters, fb.counters + 5, fb.dense_id, fb.sub_start, g, fb.parent,
             st);
     }
-    int *rootmin = reinterpret_cast<int *>(fb.tmp);
-    cudaMemsetAsync(rootmin, 0x7f, sizeof(int) * size_t(N), s);
-    {
-        JFOF_TRACE("finalize_roots", s);
-        finalize_roots_kernel<<<grid_for(N, 256), 256, 0, s>>>(spos, N, fb.parent, rootmin);
-    }
-    {
-        JFOF_TRACE("finalize_labels", s);
-        finalize_labels_kernel<<<grid_for(N, 256), 256, 0, s>>>(spos, N, fb.parent, rootmin, label);
-    }
+}
+
+void launch_link(const jfof_cells &c, const FofBuffers &fb, const LinkParams &lp, int32_t *label,
+                 const DevStatus &st, cudaStream_t s) {
+    launch_link_core(c, fb, lp, st, s);
+    launch_tail_labels(fb, c.n, label, s);
 }
 
 }  // namespace jfof

@@ -13,6 +13,8 @@ constexpr int kSubMax = kSubSide * kSubSide * kSubSide;  // 729
 constexpr uint32_t kDenseMaxM = 65535;
 constexpr int kDefaultDenseThreshold = 64;
 constexpr int kDefaultSmallThreshold = 4;
+// Output-order buckets of the label scatter (at most this many).
+constexpr int kTailBuckets = 256;
 
 // One IEEE binary32 multiply on the host (b*b for the link threshold).
 inline float host_mul(float a, float b) {
@@ -38,6 +40,7 @@ struct FofBuffers {
     uint32_t *counters;    // [6]: dense cells, medium cells, four work counters
     uint16_t *sub_start;   // [D_cap][kSubMax + 1]
     uint32_t *medium_cells;// [medium_cap]
+    uint32_t *bucket_fill; // [kTailBuckets] label-scatter bucket cursors
 };
 
 // Dense-path parameters derived on the host from (N, L, b, n, T).
@@ -59,6 +62,10 @@ int resolve_n(int64_t N, float L, float b, int32_t n_axis, int32_t *out);
 LinkParams make_link_params(int64_t N, float L, float b, int n, int S, int T);
 void launch_bin_cells(const float *pos, int64_t N, float L, int n, bool wrap, const LinkParams &lp,
                       const FofBuffers &fb, const DevStatus &st, cudaStream_t s);
+// Union-find over the cell grid (parent[] complete, not yet flattened).
+void launch_link_core(const jfof_cells &c, const FofBuffers &fb, const LinkParams &lp, const DevStatus &st,
+                      cudaStream_t s);
+// Core, then raw labels in original order.
 void launch_link(const jfof_cells &c, const FofBuffers &fb, const LinkParams &lp, int32_t *label,
                  const DevStatus &st, cudaStream_t s);
 
@@ -70,11 +77,19 @@ struct GroupBuffers {
     uint32_t *scan_tmp;
     uint32_t *seglist;  // segmented-sort list of long halos
     int64_t seglist_words;
+    int32_t *hlabel;    // [H_cap] raw label of each halo
 };
 size_t groups_layout(int64_t N, int64_t H_cap, GroupBuffers *gb, void *base);
 void launch_groups(const int32_t *label, int64_t N, int32_t min_size, int64_t H_cap, const GroupBuffers &gb,
                    int32_t *halo_id, int32_t *count, int32_t *halo_start, int32_t *members, int32_t *n_halos,
                    const DevStatus &st, cudaStream_t s);
+
+// After launch_link_core: raw labels only, or labels with the whole of a7
+// computed from the forest (same outputs as launch_link + launch_groups).
+void launch_tail_labels(const FofBuffers &fb, int64_t N, int32_t *label, cudaStream_t s);
+void launch_tail_groups(const FofBuffers &fb, int64_t N, int32_t min_size, int64_t H_cap, const GroupBuffers &gb,
+                        int32_t *label, int32_t *halo_id, int32_t *count, int32_t *halo_start, int32_t *members,
+                        int32_t *n_halos, cudaStream_t s);
 
 // Properties.
 void launch_halo_props(const float *pos, const float *vel, int64_t N, float L, bool wrap, const int32_t *halo_start,

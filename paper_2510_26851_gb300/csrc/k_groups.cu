@@ -84,6 +84,7 @@ size_t groups_layout(int64_t N, int64_t H_cap, GroupBuffers *gb, void *base) {
     g.scan_tmp = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * scan_tmp_words(big)));
     g.seglist_words = segsort_list_words(N);
     g.seglist = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * size_t(g.seglist_words)));
+    g.hlabel = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * size_t(H_cap)));
     if (gb) *gb = g;
     return off;
 }
