@@ -87,8 +87,6 @@ struct BatchCache {
 
 void destroy_batch_cache(BatchCache *c) { delete c; }
 
-void ensure_link_tables();
-
 }  // namespace jfof
 
 namespace {
@@ -162,7 +160,6 @@ int jfof_fof_batched(jfof_ctx *ctx, const float *pos, const int64_t *h_box_offse
     if (e) return e;
     if (ws_bytes < a.ws_bytes) return JFOF_ENOMEM;
     cudaSetDevice(ctx->device);
-    ensure_link_tables();
     char *base = reinterpret_cast<char *>(ws);
     DevStatus st = ctx->dev();
     if (!use_graph) {
@@ -263,7 +260,6 @@ int jfof_autotune(jfof_ctx *ctx, const float *pos, int64_t N, float L, float b, 
     }
     const int cls[][2] = {{8, 64}, {4, 64}, {8, 128}, {16, 64}, {8, 32}, {4, 96}};
     cudaSetDevice(ctx->device);
-    ensure_link_tables();
     cudaEvent_t t0, t1;
     cudaEventCreate(&t0);
     cudaEventCreate(&t1);

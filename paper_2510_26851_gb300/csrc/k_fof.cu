@@ -11,6 +11,7 @@
 //   parent     i32[N]     union-find forest over sorted slots (parent <= slot)
 //   dense_id   u32[cells] id of each dense cell (written only for them)
 //   dense_cells u32[D_cap], sub_start u16[D_cap][kSubMax+1]
+//   sub_rows   u16[D_cap][k_max^2]  occupancy rows of each dense cell's sub-cells
 //
 // Linking in two regimes.  Cells of side s >= 1.01 b guarantee that friends
 // are in the same or adjacent cells (Sec. 2.2, Algorithm 2, with the grid
@@ -204,12 +205,6 @@ __constant__ int8_t c_nb26[26][3] = {
     {-1, 0, 1},  {0, 0, 1},  {1, 0, 1},   {-1, 1, 1},  {0, 1, 1},   {1, 1, 1},   {-1, 0, 0},
     {1, -1, 0},  {0, -1, 0}, {-1, -1, 0}, {1, 1, -1},  {0, 1, -1},  {-1, 1, -1}, {1, 0, -1},
     {0, 0, -1},  {-1, 0, -1}, {1, -1, -1}, {0, -1, -1}, {-1, -1, -1}};
-
-// 62 forward sub-cell offsets of the 5x5x5 stencil (first non-zero of
-// (dz, dy, dx) positive), the 13 with all components in {-1,0,1} first;
-// filled on the host at first use.
-constexpr int kSubNear = 13;
-__constant__ int8_t c_sub62[62][3];
 
 __device__ __forceinline__ void decode_cell(uint32_t gidx, int nb, int &cx, int &cy, int &cz) {
     uint32_t brick = gidx >> 12, local = gidx & 4095u;
@@ -535,9 +530,10 @@ __global__ void __launch_bounds__(256) medium_kernel(const float4 *__restrict__ 
 // Dense cells, part 1: one warp per dense cell.  Counting sort of the cell's
 // particles by sub-cell (staged through tmp), the sub-cell table, then a
 // shared-memory union-find over the cell's sub-cells (a sub-cell is one node:
-// its members are friends), processing the 13 adjacent forward offsets for
-// every non-empty sub-cell first and the other 49 after, with the
-// (sub-cell, offset) work spread over lanes; finally
+// its members are friends): first the 3 forward face offsets of every
+// non-empty sub-cell, then the other 118 offsets of the 5x5x5 stencil from
+// the sub-cells outside the largest component, each round over the
+// (sub-cell, non-empty neighbour) tasks spread over the lanes; finally
 // parent[slot] = first slot of the slot's local component.
 constexpr int kDenseWarps = 4;
 
@@ -546,37 +542,104 @@ __device__ __forceinline__ int sub_key(float4 q, const LinkGeom &g, int cx, int 
            g.k * (sub_coord(q.y, g.inv_fine, cy, g.k) + g.k * sub_coord(q.z, g.inv_fine, cz, g.k));
 }
 
-// One round of the dense-cell local union-find: every (non-empty sub-cell,
-// forward offset O0..O0+R-1) task, spread over the lanes; a task is skipped
-// when the two sub-cells are already in one component, else the pair of
-// sub-cells is tested until its first link.
-template <int O0, int R>
-__device__ __forceinline__ void dense_round(const uint32_t *ne, int nF, int k, const uint16_t *ss, int *lp,
-                                            const float4 *__restrict__ cp, const LinkGeom &g, int lane,
-                                            const int *offs) {
-    const int total = nF * R;
-    for (int p = lane; p < total; p += 32) {
-        uint32_t e = ne[p / R];  // key | x << 10 | y << 14 | z << 18
-        int F = int(e & 1023u);
-        int o = offs[O0 + p % R];  // (dx+2) | (dy+2) << 3 | (dz+2) << 6
-        int gx = int((e >> 10) & 15u) + (o & 7) - 2, gy = int((e >> 14) & 15u) + ((o >> 3) & 7) - 2,
-            gz = int((e >> 18) & 15u) + ((o >> 6) & 7) - 2;
-        if (unsigned(gx) >= unsigned(k) || unsigned(gy) >= unsigned(k) || unsigned(gz) >= unsigned(k)) continue;
-        int G = gx + k * (gy + k * gz);
-        int g0 = ss[G], g1 = ss[G + 1];
-        if (g0 == g1) continue;
-        if (lfind(lp, F) == lfind(lp, G)) continue;
-        int f0 = ss[F], f1 = ss[F + 1];
-        bool done = false;
-        for (int a = f0; a < f1 && !done; ++a) {
-            float4 pa = cp[a];
-            for (int c = g0; c < g1; ++c) {
-                if (linked(pa, cp[c], g)) {
-                    lunite(lp, F, G);
-                    done = true;
-                    break;
+// One round of the dense-cell local union-find over (source sub-cell F,
+// offset) tasks whose sub-cell G = F + offset is non-empty.  The candidate
+// offsets of F come from the occupancy rows (bit x of rows[z*k + y] = sub-cell
+// (x, y, z) non-empty), read a row of five offsets at a time; the tasks of 32
+// sources are laid out in shared memory (a window of tcap at a time) and then
+// taken by the lanes in turn, so no lane idles on an empty neighbour.  A task
+// is skipped when F and G are already in one component, else the pair of
+// sub-cells is tested until its first link.  Offset sets (MODE):
+//   kFace  the 3 forward face offsets (+x, +y, +z)
+//   kRest  the other 118 offsets of the 5x5x5 stencil, both directions
+constexpr int kFace = 0, kRest = 1;
+
+template <int MODE>
+__device__ __forceinline__ uint32_t row_bits(const uint32_t *rows, int k, int x, int yy, int zz, int dy, int dz) {
+    if (unsigned(yy) >= unsigned(k) || unsigned(zz) >= unsigned(k)) return 0u;
+    uint32_t w = ((rows[zz * k + yy] << 2) >> x) & 31u;  // bit dx + 2 for dx in [-2, 2]
+    int ay = dy < 0 ? -dy : dy, az = dz < 0 ? -dz : dz;
+    uint32_t allow;
+    if (MODE == kFace)
+        allow = (ay + az == 0) ? 0x08u : 0x04u;
+    else if (ay == 2 || az == 2)
+        allow = 0x1Fu;  // a component of +-2: all five
+    else if (ay + az == 0)
+        allow = 0x11u;  // dx = +-2 (+-1 are faces, 0 is the sub-cell itself)
+    else if (ay + az == 1)
+        allow = 0x1Bu;  // dx = 0 is a face
+    else
+        allow = 0x1Fu;  // edges and corners
+    return w & allow;
+}
+
+// Visits the candidate rows of a source: f(dy, dz, bits).
+template <int MODE, class Fn>
+__device__ __forceinline__ void for_rows(const uint32_t *rows, int k, int x, int y, int z, Fn f) {
+    if (MODE == kFace) {
+        f(0, 0, row_bits<kFace>(rows, k, x, y, z, 0, 0));
+        f(1, 0, row_bits<kFace>(rows, k, x, y + 1, z, 1, 0));
+        f(0, 1, row_bits<kFace>(rows, k, x, y, z + 1, 0, 1));
+    } else {
+#pragma unroll 1
+        for (int dz = -2; dz <= 2; ++dz)
+#pragma unroll
+            for (int dy = -2; dy <= 2; ++dy) f(dy, dz, row_bits<kRest>(rows, k, x, y + dy, z + dz, dy, dz));
+    }
+}
+
+template <int MODE>
+__device__ void dense_round(const uint32_t *src, int nsrc, int k, const uint16_t *ss, int *lp,
+                            const float4 *__restrict__ cp, const LinkGeom &g, int lane, const uint32_t *rows,
+                            uint32_t *tasks, int tcap) {
+    for (int b0 = 0; b0 < nsrc; b0 += 32) {
+        const int i = b0 + lane;
+        const uint32_t e = i < nsrc ? src[i] : 0u;  // key | x << 10 | y << 14 | z << 18
+        const int F = int(e & 1023u), x = int((e >> 10) & 15u), y = int((e >> 14) & 15u), z = int((e >> 18) & 15u);
+        int c = 0;
+        if (i < nsrc) for_rows<MODE>(rows, k, x, y, z, [&](int, int, uint32_t bits) { c += __popc(bits); });
+        int pre = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            int v = __shfl_up_sync(0xffffffffu, pre, o);
+            if (lane >= o) pre += v;
+        }
+        const int total = __shfl_sync(0xffffffffu, pre, 31);
+        pre -= c;
+        for (int w0 = 0; w0 < total; w0 += tcap) {
+            if (i < nsrc && c > 0 && pre < w0 + tcap && pre + c > w0) {
+                int idx = pre;
+                for_rows<MODE>(rows, k, x, y, z, [&](int dy, int dz, uint32_t bits) {
+                    while (bits) {
+                        int b = __ffs(int(bits)) - 1;
+                        bits &= bits - 1u;
+                        if (idx >= w0 && idx < w0 + tcap) {
+                            int G = F + (b - 2) + k * (dy + k * dz);
+                            tasks[idx - w0] = uint32_t(F) | uint32_t(G) << 16;
+                        }
+                        ++idx;
+                    }
+                });
+            }
+            __syncwarp();
+            const int nt = min(tcap, total - w0);
+            for (int t = lane; t < nt; t += 32) {
+                uint32_t tk = tasks[t];
+                int Fs = int(tk & 0xFFFFu), G = int(tk >> 16);
+                if (lfind(lp, Fs) == lfind(lp, G)) continue;
+                int f0 = ss[Fs], f1 = ss[Fs + 1], g0 = ss[G], g1 = ss[G + 1];
+                bool done = false;
+                for (int a = f0; a < f1 && !done; ++a) {
+                    float4 pa = cp[a];
+                    for (int cc = g0; cc < g1; ++cc) {
+                        if (linked(pa, cp[cc], g)) {
+                            lunite(lp, Fs, G);
+                            done = true;
+                            break;
+                        }
+                    }
                 }
             }
+            __syncwarp();
         }
     }
 }
@@ -587,26 +650,19 @@ __global__ void __launch_bounds__(32 * kDenseWarps) dense_cells_kernel(float4 *_
                                                                        const uint32_t *__restrict__ dense_cells,
                                                                        const uint32_t *__restrict__ ndense,
                                                                        uint32_t *next, uint16_t *__restrict__ sub_start,
+                                                                       uint16_t *__restrict__ sub_rows,
                                                                        int *__restrict__ parent, LinkGeom g) {
     __shared__ int sh_cnt[kDenseWarps][kSubMax + 1];
     __shared__ uint16_t sh_ss[kDenseWarps][kSubMax + 2];
     __shared__ uint32_t sh_ne[kDenseWarps][kSubMax + 1];
-    __shared__ int sh_off[62];
-    __shared__ int sh_off2[2 * (62 - kSubNear)];
     __shared__ int sh_sz[kDenseWarps][kSubMax + 1];
+    __shared__ uint32_t sh_rows[kDenseWarps][kSubSide * kSubSide];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int *cnt = sh_cnt[w];
     uint16_t *ss = sh_ss[w];
     uint32_t *ne = sh_ne[w];
     int *sz = sh_sz[w];
-    for (int o = threadIdx.x; o < 62; o += blockDim.x)
-        sh_off[o] = (c_sub62[o][0] + 2) | ((c_sub62[o][1] + 2) << 3) | ((c_sub62[o][2] + 2) << 6);
-    for (int o = threadIdx.x; o < 62 - kSubNear; o += blockDim.x) {
-        int dx = c_sub62[kSubNear + o][0], dy = c_sub62[kSubNear + o][1], dz = c_sub62[kSubNear + o][2];
-        sh_off2[2 * o] = (dx + 2) | ((dy + 2) << 3) | ((dz + 2) << 6);
-        sh_off2[2 * o + 1] = (2 - dx) | ((2 - dy) << 3) | ((2 - dz) << 6);
-    }
-    __syncthreads();
+    uint32_t *rows = sh_rows[w];
     int64_t D = *ndense;
     if (D > g.D_cap) D = g.D_cap;
     const int k = g.k, k3 = g.k3;
@@ -617,6 +673,7 @@ __global__ void __launch_bounds__(32 * kDenseWarps) dense_cells_kernel(float4 *_
         int cx, cy, cz;
         decode_cell(gidx, g.nb, cx, cy, cz);
         for (int key = lane; key < k3; key += 32) cnt[key] = 0;
+        for (int r = lane; r < k * k; r += 32) rows[r] = 0u;
         __syncwarp();
         for (int t = lane; t < m; t += 32) {
             float4 q = spos[start + t];
@@ -652,6 +709,7 @@ __global__ void __launch_bounds__(32 * kDenseWarps) dense_cells_kernel(float4 *_
             if (c > 0) {
                 int kz = key / (k * k), ky = (key / k) % k, kx = key % k;
                 ne[pn++] = uint32_t(key) | uint32_t(kx) << 10 | uint32_t(ky) << 14 | uint32_t(kz) << 18;
+                atomicOr(&rows[ky + k * kz], 1u << kx);
             }
             pre += c;
         }
@@ -660,6 +718,7 @@ __global__ void __launch_bounds__(32 * kDenseWarps) dense_cells_kernel(float4 *_
             tab[k3] = uint16_t(m);
         }
         __syncwarp();
+        for (int r = lane; r < k * k; r += 32) sub_rows[d * (kSubSide * kSubSide) + r] = uint16_t(rows[r]);
         for (int t = lane; t < m; t += 32) {
             float4 q = stage[start + t];
             int r = atomicAdd(&cnt[sub_key(q, g, cx, cy, cz)], 1);
@@ -668,16 +727,17 @@ __global__ void __launch_bounds__(32 * kDenseWarps) dense_cells_kernel(float4 *_
         __syncwarp();
         for (int key = lane; key < k3; key += 32) cnt[key] = key;
         __syncwarp();
-        dense_round<0, kSubNear>(ne, nF, k, ss, cnt, spos + start, g, lane, sh_off);
+        dense_round<kFace>(ne, nF, k, ss, cnt, spos + start, g, lane, rows, reinterpret_cast<uint32_t *>(sz),
+                          kSubMax + 1);
         __syncwarp();
         // full compression: every sub-cell points at its root, so the finds of
         // the second round are one load deep
         for (int i = lane; i < nF; i += 32) cnt[ne[i] & 1023u] = lfind(cnt, int(ne[i] & 1023u));
         __syncwarp();
-        // The second round (offsets with a component of +-2) can only join
-        // sub-cells still in different components.  Every such pair has an end
-        // outside the largest component, so the round runs only from the
-        // sub-cells outside it, over the far offsets in both directions.
+        // The second round (every offset but the faces) can only join sub-cells
+        // still in different components.  Every such pair has an end outside
+        // the largest component, so the round runs only from the sub-cells
+        // outside it, over those offsets in both directions.
         for (int key = lane; key < k3; key += 32) sz[key] = 0;
         __syncwarp();
         for (int i = lane; i < nF; i += 32) atomicAdd(&sz[cnt[ne[i] & 1023u]], 1);
@@ -710,7 +770,7 @@ __global__ void __launch_bounds__(32 * kDenseWarps) dense_cells_kernel(float4 *_
             nmin += __popc(mask);
         }
         __syncwarp();
-        if (nmin > 0) dense_round<0, 2 * (62 - kSubNear)>(minority, nmin, k, ss, cnt, spos + start, g, lane, sh_off2);
+        if (nmin > 0) dense_round<kRest>(minority, nmin, k, ss, cnt, spos + start, g, lane, rows, ne, kSubMax + 1);
         __syncwarp();
         for (int t = lane; t < m; t += 32) {
             float4 q = spos[start + t];
@@ -721,31 +781,114 @@ __global__ void __launch_bounds__(32 * kDenseWarps) dense_cells_kernel(float4 *_
 }
 
 // ---------------------------------------------------------------------------
-// Dense cells, part 2: one warp per dense cell, its pairs with neighbours.
-// Small and medium neighbours (any direction): each neighbour particle within
-// reach of the shared face is probed against the cell's sub-cells within 2
-// sub-cells of it (lanes over sub-cells): skipped when already in one
-// component, else tested until the first link.  Dense forward neighbours:
-// every boundary sub-cell of this cell (lanes) against the neighbour's
-// sub-cells within reach, the same way.
-__global__ void __launch_bounds__(256) dense_nbr_kernel(const float4 *__restrict__ spos,
-                                                        const uint32_t *__restrict__ cell_start,
-                                                        const uint32_t *__restrict__ dense_cells,
-                                                        const uint32_t *__restrict__ ndense, uint32_t *next,
-                                                        const uint32_t *__restrict__ dense_id,
-                                                        const uint16_t *__restrict__ sub_start, LinkGeom g,
-                                                        int *parent, DevStatus st) {
-    const int lane = threadIdx.x & 31;
+// Warp task runner: every lane brings c tasks (emit(put) hands them to put in
+// a fixed order); the warp lays them out in a shared-memory window of cap
+// entries at a time and all lanes then take them in turn (work(task)).
+template <class Emit, class Work>
+__device__ __forceinline__ void warp_tasks(int c, uint32_t *buf, int cap, int lane, Emit emit, Work work) {
+    int pre = c;
+    for (int o = 1; o < 32; o <<= 1) {
+        int v = __shfl_up_sync(0xffffffffu, pre, o);
+        if (lane >= o) pre += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, pre, 31);
+    pre -= c;
+    for (int w0 = 0; w0 < total; w0 += cap) {
+        if (c > 0 && pre < w0 + cap && pre + c > w0) {
+            int idx = pre;
+            emit([&](uint32_t task) {
+                if (idx >= w0 && idx < w0 + cap) buf[idx - w0] = task;
+                ++idx;
+            });
+        }
+        __syncwarp();
+        const int nt = min(cap, total - w0);
+        for (int t = lane; t < nt; t += 32) work(buf[t]);
+        __syncwarp();
+    }
+}
+
+// Box of sub-cells, inclusive per axis.
+struct SubBox {
+    int x0, y0, z0, x1, y1, z1;
+};
+
+// Non-empty sub-cells of a dense cell (occupancy rows) inside box b: f(G)
+// for each, in a fixed order.
+template <class Fn>
+__device__ __forceinline__ void for_box(const uint16_t *rows, int k, SubBox b, Fn f) {
+    const uint32_t xm = (1u << (b.x1 - b.x0 + 1)) - 1u;
+    for (int z = b.z0; z <= b.z1; ++z)
+        for (int y = b.y0; y <= b.y1; ++y) {
+            uint32_t bits = (uint32_t(rows[z * k + y]) >> b.x0) & xm;
+            while (bits) {
+                int i = __ffs(int(bits)) - 1;
+                bits &= bits - 1u;
+                f(b.x0 + i + k * (y + k * z));
+            }
+        }
+}
+
+__device__ __forceinline__ int box_count(const uint16_t *rows, int k, SubBox b) {
+    const uint32_t xm = (1u << (b.x1 - b.x0 + 1)) - 1u;
+    int c = 0;
+    for (int z = b.z0; z <= b.z1; ++z)
+        for (int y = b.y0; y <= b.y1; ++y) c += __popc((uint32_t(rows[z * k + y]) >> b.x0) & xm);
+    return c;
+}
+
+// Box within 2 sub-cells of position (cx, cy, cz) (may lie outside the cell),
+// clipped to the cell; false when empty.
+__device__ __forceinline__ bool near_box(int cx, int cy, int cz, int k, SubBox &b) {
+    b.x0 = max(cx - 2, 0);
+    b.y0 = max(cy - 2, 0);
+    b.z0 = max(cz - 2, 0);
+    b.x1 = min(cx + 2, k - 1);
+    b.y1 = min(cy + 2, k - 1);
+    b.z1 = min(cz + 2, k - 1);
+    return b.x0 <= b.x1 && b.y0 <= b.y1 && b.z0 <= b.z1;
+}
+
+// Dense cells, part 2: one warp per dense cell A, its pairs with neighbours.
+//   small / medium neighbour B (any direction): each particle q of B within
+//   reach of A is paired with the non-empty sub-cells of A within 2 sub-cells
+//   of q's position
+//   dense forward neighbour B: each non-empty sub-cell F of A in the two
+//   layers facing B is paired with the non-empty sub-cells of B within 2
+//   sub-cells of F
+// The (source, sub-cell) tasks come from the occupancy rows of the two cells
+// and are spread over the lanes; a task is skipped when its two ends are
+// already in one component, else tested until the first link.
+constexpr int kNbrWarps = 8;
+constexpr int kNbrTaskCap = 512;
+constexpr int kNbrSrcCap = 2 * kSubSide * kSubSide;
+
+__global__ void __launch_bounds__(32 * kNbrWarps) dense_nbr_kernel(const float4 *__restrict__ spos,
+                                                                   const uint32_t *__restrict__ cell_start,
+                                                                   const uint32_t *__restrict__ dense_cells,
+                                                                   const uint32_t *__restrict__ ndense, uint32_t *next,
+                                                                   const uint32_t *__restrict__ dense_id,
+                                                                   const uint16_t *__restrict__ sub_start,
+                                                                   const uint16_t *__restrict__ sub_rows, LinkGeom g,
+                                                                   int *parent, DevStatus st) {
+    __shared__ uint32_t sh_task[kNbrWarps][kNbrTaskCap];
+    __shared__ uint32_t sh_src[kNbrWarps][kNbrSrcCap];
+    __shared__ float4 sh_q[kNbrWarps][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t *tasks = sh_task[w];
+    uint32_t *srcl = sh_src[w];
+    float4 *qbuf = sh_q[w];
     int64_t D = *ndense;
     if (D > g.D_cap) D = g.D_cap;
-    const int k = g.k;
+    const int k = g.k, kk = k * k;
     for (int64_t d = next_task(next, lane); d < D; d = next_task(next, lane)) {
         if (g.n < 3) break;
         uint32_t ga = dense_cells[d];
         int cx, cy, cz;
         decode_cell(ga, g.nb, cx, cy, cz);
-        uint32_t a0 = cell_start[ga];
+        const uint32_t a0 = cell_start[ga];
         const uint16_t *ta = sub_start + d * (kSubMax + 1);
+        const uint16_t *ra = sub_rows + d * (kSubSide * kSubSide);
         uint32_t nb0 = 0, nb1 = 0, nid = 0;
         int ncls = 0;
         if (lane < 26) {
@@ -759,121 +902,118 @@ __global__ void __launch_bounds__(256) dense_nbr_kernel(const float4 *__restrict
         for (int o = 0; o < 26; ++o) {
             int cls = __shfl_sync(0xffffffffu, ncls, o);
             if (cls == 0 || (cls == 3 && o >= 13)) continue;
-            uint32_t b0 = __shfl_sync(0xffffffffu, nb0, o), b1 = __shfl_sync(0xffffffffu, nb1, o);
-            int off[3] = {c_nb26[o][0], c_nb26[o][1], c_nb26[o][2]};
-            int bx = wrapc(cx + off[0], g.n), by = wrapc(cy + off[1], g.n), bz = wrapc(cz + off[2], g.n);
+            const uint32_t b0 = __shfl_sync(0xffffffffu, nb0, o), b1 = __shfl_sync(0xffffffffu, nb1, o);
+            const int off[3] = {c_nb26[o][0], c_nb26[o][1], c_nb26[o][2]};
+            const int bx = wrapc(cx + off[0], g.n), by = wrapc(cy + off[1], g.n), bz = wrapc(cz + off[2], g.n);
             if (cls != 3) {
-                int mB = int(b1 - b0);
+                const int mB = int(b1 - b0);
                 for (int cb = 0; cb < mB; cb += 32) {
-                    int j = cb + lane;
-                    float4 qb = make_float4(0.f, 0.f, 0.f, 0.f);
+                    const int j = cb + lane;
+                    float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
                     bool inb = j < mB;
+                    SubBox bx3{0, 0, 0, -1, -1, -1};
                     if (inb) {
-                        qb = spos[b0 + j];
-                        inb = gap_to_neighbour(qb, bx, by, bz, -off[0], -off[1], -off[2], g.cell_side) <= g.gap2;
+                        q = spos[b0 + j];
+                        inb = gap_to_neighbour(q, bx, by, bz, -off[0], -off[1], -off[2], g.cell_side) <= g.gap2;
                     }
-                    unsigned bits = __ballot_sync(0xffffffffu, inb);
-                    while (bits) {
-                        int src = __ffs(bits) - 1;
-                        bits &= bits - 1;
-                        float4 q = shfl4(qb, src);
-                        int lq[3] = {sub_coord(q.x, g.inv_fine, bx, k), sub_coord(q.y, g.inv_fine, by, k),
-                                     sub_coord(q.z, g.inv_fine, bz, k)};
-                        int lo[3], n3[3];
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            int c = lq[a] + off[a] * k;  // q's sub-cell in this cell's frame
-                            lo[a] = max(c - 2, 0);
-                            n3[a] = min(c + 2, k - 1) - lo[a] + 1;
-                        }
-                        if (n3[0] <= 0 || n3[1] <= 0 || n3[2] <= 0) continue;
-                        int nbox = n3[0] * n3[1] * n3[2];
-                        int qs = int(b0 + cb + src);
-                        for (int t = lane; t < nbox; t += 32) {
-                            int G = (lo[0] + t % n3[0]) + k * ((lo[1] + (t / n3[0]) % n3[1]) + k * (lo[2] + t / (n3[0] * n3[1])));
-                            uint32_t c0 = ta[G], c1 = ta[G + 1];
-                            if (c0 == c1) continue;
-                            if (uf_find(parent, qs) == uf_find(parent, int(a0 + c0))) continue;
-                            for (uint32_t c = c0; c < c1; ++c)
-                                if (linked(q, spos[a0 + c], g)) {
-                                    uf_unite(parent, qs, int(a0 + c), st);
+                    if (inb) {
+                        // q's sub-cell in A's frame, and the box of A's sub-cells within 2 of it
+                        inb = near_box(sub_coord(q.x, g.inv_fine, bx, k) + off[0] * k,
+                                       sub_coord(q.y, g.inv_fine, by, k) + off[1] * k,
+                                       sub_coord(q.z, g.inv_fine, bz, k) + off[2] * k, k, bx3);
+                    }
+                    if (!__any_sync(0xffffffffu, inb)) continue;
+                    qbuf[lane] = q;
+                    const int c = inb ? box_count(ra, k, bx3) : 0;
+                    __syncwarp();
+                    warp_tasks(
+                        c, tasks, kNbrTaskCap, lane,
+                        [&](auto put) { for_box(ra, k, bx3, [&](int G) { put(uint32_t(lane) | uint32_t(G) << 5); }); },
+                        [&](uint32_t t) {
+                            const int qi = int(t & 31u), G = int(t >> 5);
+                            const int qs = int(b0) + cb + qi;
+                            const uint32_t c0 = ta[G], c1 = ta[G + 1];
+                            if (uf_find(parent, qs) == uf_find(parent, int(a0 + c0))) return;
+                            const float4 qq = qbuf[qi];
+                            for (uint32_t cc = c0; cc < c1; ++cc)
+                                if (linked(qq, spos[a0 + cc], g)) {
+                                    uf_unite(parent, qs, int(a0 + cc), st);
                                     break;
                                 }
-                        }
-                    }
+                        });
                 }
                 continue;
             }
-            const uint16_t *tb = sub_start + int64_t(__shfl_sync(0xffffffffu, nid, o)) * (kSubMax + 1);
-            int flo[3], fn[3];
+            const int64_t db = int64_t(__shfl_sync(0xffffffffu, nid, o));
+            const uint16_t *tb = sub_start + db * (kSubMax + 1);
+            const uint16_t *rb = sub_rows + db * (kSubSide * kSubSide);
+            // sources: the non-empty sub-cells of A in the two layers facing B
+            int slo[3], shi[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                flo[a] = off[a] > 0 ? k - 2 : 0;
-                fn[a] = off[a] != 0 ? 2 : k;
+                slo[a] = off[a] > 0 ? k - 2 : 0;
+                shi[a] = off[a] < 0 ? 1 : k - 1;
             }
-            int nFb = fn[0] * fn[1] * fn[2];
-            for (int f = lane; f < nFb; f += 32) {
-                int fc[3] = {flo[0] + f % fn[0], flo[1] + (f / fn[0]) % fn[1], flo[2] + f / (fn[0] * fn[1])};
-                int F = fc[0] + k * (fc[1] + k * fc[2]);
-                uint32_t f0 = ta[F], f1 = ta[F + 1];
-                if (f0 == f1) continue;
-                int lo[3], hi[3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    int c = fc[a] - off[a] * k;
-                    lo[a] = max(c - 2, 0);
-                    hi[a] = min(c + 2, k - 1);
+            int nsrc = 0;
+            for (int r0 = 0; r0 < kk; r0 += 32) {
+                const int r = r0 + lane;
+                const int y = r % k, z = r / k;
+                uint32_t bits = 0u;
+                if (r < kk && y >= slo[1] && y <= shi[1] && z >= slo[2] && z <= shi[2])
+                    bits = (uint32_t(ra[r]) >> slo[0]) & ((1u << (shi[0] - slo[0] + 1)) - 1u);
+                int c = __popc(bits), pre = c;
+                for (int sh = 1; sh < 32; sh <<= 1) {
+                    int v = __shfl_up_sync(0xffffffffu, pre, sh);
+                    if (lane >= sh) pre += v;
                 }
-                for (int zz = lo[2]; zz <= hi[2]; ++zz)
-                    for (int yy = lo[1]; yy <= hi[1]; ++yy)
-                        for (int xx = lo[0]; xx <= hi[0]; ++xx) {
-                            int G = xx + k * (yy + k * zz);
-                            uint32_t c0 = tb[G], c1 = tb[G + 1];
-                            if (c0 == c1) continue;
-                            if (uf_find(parent, int(a0 + f0)) == uf_find(parent, int(b0 + c0))) continue;
-                            bool done = false;
-                            for (uint32_t a = f0; a < f1 && !done; ++a) {
-                                float4 p = spos[a0 + a];
-                                for (uint32_t c = c0; c < c1; ++c)
-                                    if (linked(p, spos[b0 + c], g)) {
-                                        uf_unite(parent, int(a0 + a), int(b0 + c), st);
-                                        done = true;
-                                        break;
-                                    }
-                            }
-                        }
+                int idx = nsrc + pre - c;
+                while (bits) {
+                    int b = __ffs(int(bits)) - 1;
+                    bits &= bits - 1u;
+                    int x = slo[0] + b;
+                    srcl[idx++] = uint32_t(x) | uint32_t(y) << 4 | uint32_t(z) << 8;
+                }
+                nsrc += __shfl_sync(0xffffffffu, pre, 31);
             }
+            __syncwarp();
+            for (int s0 = 0; s0 < nsrc; s0 += 32) {
+                const int i = s0 + lane;
+                int F = 0;
+                SubBox fb3{0, 0, 0, -1, -1, -1};
+                bool has = i < nsrc;
+                if (has) {
+                    uint32_t e = srcl[i];
+                    int fx = int(e & 15u), fy = int((e >> 4) & 15u), fz = int((e >> 8) & 15u);
+                    F = fx + k * (fy + k * fz);
+                    // F's position in B's frame, and B's sub-cells within 2 of it
+                    has = near_box(fx - off[0] * k, fy - off[1] * k, fz - off[2] * k, k, fb3);
+                }
+                const int c = has ? box_count(rb, k, fb3) : 0;
+                warp_tasks(
+                    c, tasks, kNbrTaskCap, lane,
+                    [&](auto put) { for_box(rb, k, fb3, [&](int G) { put(uint32_t(F) | uint32_t(G) << 16); }); },
+                    [&](uint32_t t) {
+                        const int Fs = int(t & 0xFFFFu), G = int(t >> 16);
+                        const uint32_t f0 = ta[Fs], f1 = ta[Fs + 1], c0 = tb[G], c1 = tb[G + 1];
+                        if (uf_find(parent, int(a0 + f0)) == uf_find(parent, int(b0 + c0))) return;
+                        bool done = false;
+                        for (uint32_t a = f0; a < f1 && !done; ++a) {
+                            const float4 p = spos[a0 + a];
+                            for (uint32_t cc = c0; cc < c1; ++cc)
+                                if (linked(p, spos[b0 + cc], g)) {
+                                    uf_unite(parent, int(a0 + a), int(b0 + cc), st);
+                                    done = true;
+                                    break;
+                                }
+                        }
+                    });
+            }
+            __syncwarp();
         }
     }
 }
 
 // ---------------------------------------------------------------------------
-static bool g_sub62_ready[64] = {};
-
-// Fills the constant sub-cell offset table of the current device (a
-// synchronous copy: call outside stream capture).
-void ensure_link_tables() {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64 || g_sub62_ready[dev]) return;
-    int8_t t[62][3];
-    int c = 0;
-    for (int pass = 0; pass < 2; ++pass)
-        for (int dz = -2; dz <= 2; ++dz)
-            for (int dy = -2; dy <= 2; ++dy)
-                for (int dx = -2; dx <= 2; ++dx) {
-                    bool fwd = dz > 0 || (dz == 0 && (dy > 0 || (dy == 0 && dx > 0)));
-                    bool near = dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1;
-                    if (!fwd || near != (pass == 0)) continue;
-                    t[c][0] = int8_t(dx);
-                    t[c][1] = int8_t(dy);
-                    t[c][2] = int8_t(dz);
-                    ++c;
-                }
-    cudaMemcpyToSymbol(c_sub62, t, sizeof(t));
-    g_sub62_ready[dev] = true;
-}
-
 LinkParams make_link_params(int64_t N, float L, float b, int n, int S, int T) {
     LinkParams lp{};
     double s = double(L) / n;
@@ -894,7 +1034,6 @@ LinkParams make_link_params(int64_t N, float L, float b, int n, int S, int T) {
 void launch_link_core(const jfof_cells &c, const FofBuffers &fb, const LinkParams &lp, const DevStatus &st,
                       cudaStream_t s) {
     int64_t N = c.n;
-    ensure_link_tables();
     float b2 = host_mul(c.b, c.b);
     double gap = 1.02 * double(c.b);
     LinkGeom g{c.L, 0.5f * c.L, b2, float(double(c.n_axis) / double(c.L)), lp.inv_fine,
@@ -910,7 +1049,8 @@ void launch_link_core(const jfof_cells &c, const FofBuffers &fb, const LinkParam
     if (lp.T > 0) {
         JFOF_TRACE("dense_cells", s);
         dense_cells_kernel<<<grid_for(lp.D_cap * 32, 32 * kDenseWarps, 8), 32 * kDenseWarps, 0, s>>>(
-            fb.spos, fb.tmp, c.cell_start, fb.dense_cells, fb.counters, fb.counters + 2, fb.sub_start, fb.parent, g);
+            fb.spos, fb.tmp, c.cell_start, fb.dense_cells, fb.counters, fb.counters + 2, fb.sub_start, fb.sub_rows,
+            fb.parent, g);
     }
     {
         JFOF_TRACE("link_medium_local", s);
@@ -930,9 +1070,9 @@ void launch_link_core(const jfof_cells &c, const FofBuffers &fb, const LinkParam
     }
     if (lp.T > 0) {
         JFOF_TRACE("link_dense_nbr", s);
-        dense_nbr_kernel<<<grid_for(lp.D_cap * 32, 256, 8), 256, 0, s>>>(
-            spos, c.cell_start, fb.dense_cells, fb.counters, fb.counters + 5, fb.dense_id, fb.sub_start, g, fb.parent,
-            st);
+        dense_nbr_kernel<<<grid_for(lp.D_cap * 32, 32 * kNbrWarps, 8), 32 * kNbrWarps, 0, s>>>(
+            spos, c.cell_start, fb.dense_cells, fb.counters, fb.counters + 5, fb.dense_id, fb.sub_start, fb.sub_rows,
+            g, fb.parent, st);
     }
 }
 

@@ -39,6 +39,7 @@ struct FofBuffers {
     uint32_t *dense_cells; // [D_cap]
     uint32_t *counters;    // [6]: dense cells, medium cells, four work counters
     uint16_t *sub_start;   // [D_cap][kSubMax + 1]
+    uint16_t *sub_rows;    // [D_cap][kSubSide^2] bit x of row (y, z): sub-cell non-empty
     uint32_t *medium_cells;// [medium_cap]
     uint32_t *bucket_fill; // [kTailBuckets] label-scatter bucket cursors
 };
