@@ -437,25 +437,59 @@ __global__ void __launch_bounds__(32 * kMedWarps) medium_local_kernel(const floa
     }
 }
 
-// Medium cells, cross part: one warp per cell.  For each small neighbour
-// (any direction) and each medium forward neighbour, the particles of both
-// cells that lie within reach of the shared face/edge/corner are selected by
-// ballot and their cross pairs spread over lanes.
-__global__ void __launch_bounds__(256) medium_kernel(const float4 *__restrict__ spos,
-                                                     const uint32_t *__restrict__ cell_start,
-                                                     const uint32_t *__restrict__ medium_cells,
-                                                     const uint32_t *__restrict__ nmedium, uint32_t *next,
-                                                     const uint32_t *__restrict__ dense_id, int64_t M_cap,
-                                                     LinkGeom g, int *parent, DevStatus st) {
-    const int lane = threadIdx.x & 31;
+// Medium cells, cross part: one warp per cell A.  Every particle of a small
+// neighbour (any direction) or a medium forward neighbour that lies within
+// reach of A is gathered, with the offset of its cell, into a shared-memory
+// list (the neighbours' particles are spread over the lanes as one flat
+// range); the list is then swept by the whole warp, each lane pairing its
+// particles of A that reach that offset (a 26-bit mask per particle) with
+// each entry.  Cached component representatives: equal values mean one
+// component, so such a linked pair needs no union; after a union every cached
+// value naming either side becomes the merged representative (a stale value
+// only costs an exact union).  A cell of more than 64 particles (possible
+// only when it cannot take the dense path) walks its neighbours one at a
+// time instead.
+constexpr int kMedXWarps = 8;
+constexpr int kMedList = 64;
+
+// Offsets o in cand whose neighbour cell p can reach (gap <= 1.02 b).
+__device__ __forceinline__ uint32_t reach_mask(float4 p, int cx, int cy, int cz, uint32_t cand, const LinkGeom &g) {
+    uint32_t m = 0u;
+    while (cand) {
+        const int o = __ffs(int(cand)) - 1;
+        cand &= cand - 1u;
+        if (gap_to_neighbour(p, cx, cy, cz, c_nb26[o][0], c_nb26[o][1], c_nb26[o][2], g.cell_side) <= g.gap2)
+            m |= 1u << o;
+    }
+    return m;
+}
+
+__global__ void __launch_bounds__(32 * kMedXWarps) medium_kernel(const float4 *__restrict__ spos,
+                                                                 const uint32_t *__restrict__ cell_start,
+                                                                 const uint32_t *__restrict__ medium_cells,
+                                                                 const uint32_t *__restrict__ nmedium,
+                                                                 uint32_t *next,
+                                                                 const uint32_t *__restrict__ dense_id,
+                                                                 int64_t M_cap, LinkGeom g, int *parent,
+                                                                 DevStatus st) {
+    __shared__ float4 sh_q[kMedXWarps][kMedList];
+    __shared__ int sh_slot[kMedXWarps][kMedList];
+    __shared__ int sh_rep[kMedXWarps][kMedList];
+    __shared__ int sh_pre[kMedXWarps][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float4 *lq = sh_q[w];
+    int *lslot = sh_slot[w], *lrep = sh_rep[w], *pre = sh_pre[w];
+    // this lane's neighbour offset (lanes < 26), packed for shuffles
+    const int my_off = lane < 26 ? (c_nb26[lane][0] + 1) | (c_nb26[lane][1] + 1) << 2 | (c_nb26[lane][2] + 1) << 4
+                                 : 0;
     int64_t M = *nmedium;
     if (M > M_cap) M = M_cap;
     for (int64_t t = next_task(next, lane); t < M; t = next_task(next, lane)) {
         uint32_t ga = medium_cells[t];
         int cx, cy, cz;
         decode_cell(ga, g.nb, cx, cy, cz);
-        uint32_t a0 = cell_start[ga];
-        int mA = int(cell_start[ga + 1] - a0);
+        const uint32_t a0 = cell_start[ga];
+        const int mA = int(cell_start[ga + 1] - a0);
         if (g.n < 3) continue;
         uint32_t nb0 = 0, nb1 = 0;
         int ncls = 0;
@@ -466,13 +500,89 @@ __global__ void __launch_bounds__(256) medium_kernel(const float4 *__restrict__ 
             nb1 = cell_start[gb + 1];
             ncls = cell_class(nb1 - nb0, gb, g, dense_id);
         }
-        // Cached component representatives of the cell's first 64 particles
-        // (lane holds particles lane and lane+32).  Equal representatives
-        // mean one component, so such a linked pair needs no union; after a
-        // union every cached value naming either side becomes the merged
-        // representative.  A stale value only costs an exact union.
         int rep0 = lane < mA ? uf_find(parent, int(a0 + lane)) : -1;
         int rep1 = lane + 32 < mA ? uf_find(parent, int(a0 + lane + 32)) : -1;
+        if (mA <= 64) {
+            const float4 pa0 = lane < mA ? spos[a0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 pa1 = lane + 32 < mA ? spos[a0 + lane + 32] : make_float4(0.f, 0.f, 0.f, 0.f);
+            // neighbours to visit: small cells all round, medium forward
+            const uint32_t cand = __ballot_sync(0xffffffffu, lane < 26 && (ncls == 1 || (ncls == 2 && lane < 13)));
+            const uint32_t m0 = lane < mA ? reach_mask(pa0, cx, cy, cz, cand, g) : 0u;
+            const uint32_t m1 = lane + 32 < mA ? reach_mask(pa1, cx, cy, cz, cand, g) : 0u;
+            const uint32_t reach = __reduce_or_sync(0xffffffffu, m0 | m1);
+            const bool take = (reach >> lane) & 1u;
+            const int c = take ? int(nb1 - nb0) : 0;
+            int incl = c;
+            for (int o = 1; o < 32; o <<= 1) {
+                int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            pre[lane] = incl;
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            __syncwarp();
+            int nl = 0;
+            for (int t0 = 0; t0 < total; t0 += 32) {
+                const int tt = t0 + lane;
+                // owner neighbour: number of inclusive prefixes <= tt
+                int o = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1)
+                    if (pre[o + step - 1] <= tt) o += step;
+                const int src = tt < total ? o : 0;
+                const uint32_t ob0 = __shfl_sync(0xffffffffu, nb0, src);
+                const int opk = __shfl_sync(0xffffffffu, my_off, src);
+                const int ex = __shfl_sync(0xffffffffu, incl - c, src);
+                bool inb = tt < total;
+                float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+                int qs = 0;
+                if (inb) {
+                    const int ox = (opk & 3) - 1, oy = ((opk >> 2) & 3) - 1, oz = ((opk >> 4) & 3) - 1;
+                    qs = int(ob0) + (tt - ex);
+                    q = spos[qs];
+                    inb = gap_to_neighbour(q, wrapc(cx + ox, g.n), wrapc(cy + oy, g.n), wrapc(cz + oz, g.n), -ox, -oy,
+                                           -oz, g.cell_side) <= g.gap2;
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, inb);
+                if (inb) {
+                    int pos = nl + __popc(bal & ((1u << lane) - 1u));
+                    lq[pos] = make_float4(q.x, q.y, q.z, __int_as_float(src));
+                    lslot[pos] = qs;
+                }
+                nl += __popc(bal);
+                __syncwarp();
+                if (nl > kMedList - 32 || (t0 + 32 >= total && nl > 0)) {
+                    // sweep the list: every lane pairs its particles of A with each entry
+                    for (int e = lane; e < nl; e += 32) lrep[e] = uf_find(parent, lslot[e]);
+                    __syncwarp();
+                    for (int e = 0; e < nl; ++e) {
+                        const float4 qe = lq[e];
+                        const int qse = lslot[e], oe = __float_as_int(qe.w);
+                        int rb = lrep[e];
+                        const int nh = mA > 32 ? 2 : 1;
+                        for (int h = 0; h < nh; ++h) {
+                            const uint32_t mh = h ? m1 : m0;
+                            const int ra = h ? rep1 : rep0;
+                            const bool join = ((mh >> oe) & 1u) && ra != rb && linked(h ? pa1 : pa0, qe, g);
+                            const int merged = join ? uf_unite_rep(parent, int(a0) + lane + 32 * h, qse, st) : 0;
+                            unsigned um = __ballot_sync(0xffffffffu, join);
+                            const int s2 = rb;
+                            while (um) {
+                                const int L = __ffs(um) - 1;
+                                um &= um - 1u;
+                                const int s1 = __shfl_sync(0xffffffffu, ra, L);
+                                const int nr = __shfl_sync(0xffffffffu, merged, L);
+                                if (rep0 == s1 || rep0 == s2) rep0 = nr;
+                                if (rep1 == s1 || rep1 == s2) rep1 = nr;
+                                if (rb == s1 || rb == s2) rb = nr;
+                            }
+                        }
+                    }
+                    __syncwarp();
+                    nl = 0;
+                }
+            }
+            continue;
+        }
         for (int o = 0; o < 26; ++o) {
             int cls = __shfl_sync(0xffffffffu, ncls, o);
             if (cls == 0 || cls == 3 || (cls == 2 && o >= 13)) continue;
@@ -1064,7 +1174,7 @@ void launch_link_core(const jfof_cells &c, const FofBuffers &fb, const LinkParam
     }
     {
         JFOF_TRACE("link_medium", s);
-        medium_kernel<<<grid_for(medium_cap(N) * 32, 256, 8), 256, 0, s>>>(
+        medium_kernel<<<grid_for(medium_cap(N) * 32, 32 * kMedXWarps, 8), 32 * kMedXWarps, 0, s>>>(
             spos, c.cell_start, fb.medium_cells, fb.counters + 1, fb.counters + 4, fb.dense_id, medium_cap(N), g,
             fb.parent, st);
     }
