@@ -270,8 +270,14 @@ __global__ void iota_kernel(int *__restrict__ p, int64_t N) {
 // ---------------------------------------------------------------------------
 // Small cells: one thread per particle.  Pairs with later particles of its
 // cell and with every particle of a small forward neighbour cell that lies
-// within reach (the particle's gap to that cell <= 1.02 b).  All loops are
-// bounded by S.
+// within reach (the particle's gap to that cell <= 1.02 b).  The 13 forward
+// offsets are compile-time constants here (packed 2 bits per offset and
+// axis, value + 1), so the reach test of each is two adds and a compare on the
+// particle's squared gaps to its cell's six faces.  All loops are bounded by S.
+constexpr uint32_t kFwdX = 0x2492492u, kFwdY = 0x2a540a9u, kFwdZ = 0x2aaaa55u;
+
+__device__ __forceinline__ int fwd_comp(uint32_t packed, int o) { return int((packed >> (2 * o)) & 3u) - 1; }
+
 __global__ void __launch_bounds__(256) small_kernel(const float4 *__restrict__ spos,
                                                     const uint32_t *__restrict__ cell_start, int64_t N, LinkGeom g,
                                                     int *parent, DevStatus st) {
@@ -285,10 +291,28 @@ __global__ void __launch_bounds__(256) small_kernel(const float4 *__restrict__ s
         for (uint32_t j = uint32_t(s) + 1; j < a1; ++j)
             if (linked(p, spos[j], g)) uf_unite(parent, int(s), int(j), st);
         if (g.n < 3) continue;
-#pragma unroll 1
+        // squared gaps to the low and high faces of the cell (as in gap_to_neighbour)
+        float lx = fmaxf(p.x - float(cx) * g.cell_side, 0.f), hx = fmaxf(float(cx + 1) * g.cell_side - p.x, 0.f);
+        float ly = fmaxf(p.y - float(cy) * g.cell_side, 0.f), hy = fmaxf(float(cy + 1) * g.cell_side - p.y, 0.f);
+        float lz = fmaxf(p.z - float(cz) * g.cell_side, 0.f), hz = fmaxf(float(cz + 1) * g.cell_side - p.z, 0.f);
+        lx *= lx;
+        hx *= hx;
+        ly *= ly;
+        hy *= hy;
+        lz *= lz;
+        hz *= hz;
+        uint32_t cand = 0u;
+#pragma unroll
         for (int o = 0; o < 13; ++o) {
-            int ox = c_nb26[o][0], oy = c_nb26[o][1], oz = c_nb26[o][2];
-            if (gap_to_neighbour(p, cx, cy, cz, ox, oy, oz, g.cell_side) > g.gap2) continue;
+            const int ox = fwd_comp(kFwdX, o), oy = fwd_comp(kFwdY, o), oz = fwd_comp(kFwdZ, o);
+            float d = (ox > 0 ? hx : (ox < 0 ? lx : 0.f)) + (oy > 0 ? hy : (oy < 0 ? ly : 0.f)) +
+                      (oz > 0 ? hz : (oz < 0 ? lz : 0.f));
+            if (d <= g.gap2) cand |= 1u << o;
+        }
+        while (cand) {
+            const int o = __ffs(int(cand)) - 1;
+            cand &= cand - 1u;
+            const int ox = fwd_comp(kFwdX, o), oy = fwd_comp(kFwdY, o), oz = fwd_comp(kFwdZ, o);
             uint64_t nb = cell_table_index(wrapc(cx + ox, g.n), wrapc(cy + oy, g.n), wrapc(cz + oz, g.n), g.nb);
             uint32_t b0 = cell_start[nb], b1 = cell_start[nb + 1];
             if (b1 - b0 > uint32_t(g.S)) continue;  // medium/dense neighbours handle this pair

@@ -12,7 +12,7 @@ constexpr int kSubSide = 9;
 constexpr int kSubMax = kSubSide * kSubSide * kSubSide;  // 729
 constexpr uint32_t kDenseMaxM = 65535;
 constexpr int kDefaultDenseThreshold = 64;
-constexpr int kDefaultSmallThreshold = 4;
+constexpr int kDefaultSmallThreshold = 8;
 // Output-order buckets of the label scatter (at most this many).
 constexpr int kTailBuckets = 256;
 
