@@ -105,7 +105,10 @@ int jfof_set_cell_classes(jfof_ctx *ctx, int32_t small_max, int32_t dense_over);
 /* Largest legal n for (L, b), capped at 1600. */
 int jfof_max_cells_per_axis(float L, float b, int32_t *n_axis);
 
-/* Default n for N particles: the largest legal n with n^3 <= N (at least 1). */
+/* Default n for N particles: the largest legal n with n^3 <= N (at least 1),
+   raised by up to max(2, n/8) when that is the smallest n at which the cells
+   are narrow enough for the sub-cell path of dense cells (at most 9
+   sub-cells of side <= b/(1.02 sqrt 3) per cell side). */
 int jfof_default_cells_per_axis(int64_t N, float L, float b, int32_t *n_axis);
 
 /* ---------------------------------------------------------------------- */

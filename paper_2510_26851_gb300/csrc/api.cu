@@ -35,6 +35,17 @@ int resolve_n(int64_t N, float L, float b, int32_t n_axis, int32_t *out) {
     if (n_axis == 0) {
         int32_t n = nmax;
         while (n > 3 && double(n) * n * n > double(N)) --n;
+        // When cells of that size are too wide for the sub-cell path of dense
+        // cells (more than kSubSide sub-cells per side), take the next few
+        // sizes up: one more cell per axis usually brings it back.
+        const int32_t hi = n + (n / 8 > 2 ? n / 8 : 2);
+        for (int32_t m = n; m <= hi && m <= nmax; ++m) {
+            if (m < 5) break;
+            if (make_link_params(N, L, b, m, kDefaultSmallThreshold, kDefaultDenseThreshold).T > 0) {
+                n = m;
+                break;
+            }
+        }
         *out = n;
         return JFOF_OK;
     }
@@ -71,7 +82,10 @@ size_t fof_layout(int64_t N, int n, FofBuffers *fb, void *base) {
     f.brick_count = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * size_t(n_bricks + 1)));
     f.brick_start = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * size_t(n_bricks + 1)));
     f.cursor = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * size_t(n_bricks + 1)));
-    f.scan_tmp = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * scan_tmp_words(n_bricks)));
+    const int64_t few = n_bricks <= kFewBricks ? n_bricks * kFewGrid : 0;
+    f.scan_tmp = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * scan_tmp_words(few > n_bricks ? few : n_bricks)));
+    f.bin_mat = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * size_t(few)));
+    f.bin_base = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * size_t(few + 1)));
     // bin scatter buffer; dense-cell staging; then the link's rootmin[N]
     f.tmp = reinterpret_cast<float4 *>(take(sizeof(float4) * size_t(N)));
     f.parent = reinterpret_cast<int *>(take(sizeof(int) * size_t(N)));

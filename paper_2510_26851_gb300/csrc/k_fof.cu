@@ -63,15 +63,90 @@ __global__ void __launch_bounds__(256) bin_count_kernel(const float *__restrict_
 
 // Pass 2: scatter each particle to its brick's segment of tmp (the brick
 // cursors and partially written lines stay in L2, which combines the writes).
+// Four particles per thread per step, so four cursor atomics are in flight
+// before the first result is needed.
+constexpr int kScatterItems = 4;
+
 __global__ void __launch_bounds__(256) bin_scatter_kernel(const float *__restrict__ pos, int64_t N, BinGeom g,
                                                           uint32_t *__restrict__ cursor, float4 *__restrict__ tmp,
                                                           DevStatus st) {
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i0 < N; i0 += stride * kScatterItems) {
+        float x[kScatterItems], y[kScatterItems], z[kScatterItems];
+        uint32_t slot[kScatterItems];
+#pragma unroll
+        for (int u = 0; u < kScatterItems; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i < N) load_particle(pos, i, g, st, x[u], y[u], z[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < kScatterItems; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i >= N) continue;
+            int ix = cell_coord(x[u], g.inv_cell, g.n), iy = cell_coord(y[u], g.inv_cell, g.n),
+                iz = cell_coord(z[u], g.inv_cell, g.n);
+            uint64_t brick = uint64_t(ix >> 4) + uint64_t(g.nb) * (uint64_t(iy >> 4) + uint64_t(g.nb) * uint64_t(iz >> 4));
+            slot[u] = atomicAdd(&cursor[brick], 1u);
+        }
+#pragma unroll
+        for (int u = 0; u < kScatterItems; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i < N) tmp[slot[u]] = make_float4(x[u], y[u], z[u], __int_as_float(int(i)));
+        }
+    }
+}
+
+// Passes 1-2 for grids of at most kFewBricks bricks (small boxes), where a
+// few hundred brick counters would each take thousands of atomics: a plain
+// two-pass counting sort instead.  Each of the kFewGrid CTAs owns a
+// contiguous chunk of particles and writes its per-brick counts (one row of
+// mat); a scan of mat in brick-major order gives every (brick, CTA) pair the
+// start of its run (and every brick its start, at stride kFewGrid); the
+// scatter then ranks particles inside the CTA's runs with shared counters.
+constexpr int kFewThreads = 256;
+
+__device__ __forceinline__ uint32_t brick_of(float x, float y, float z, const BinGeom &g) {
+    int ix = cell_coord(x, g.inv_cell, g.n), iy = cell_coord(y, g.inv_cell, g.n), iz = cell_coord(z, g.inv_cell, g.n);
+    return uint32_t(ix >> 4) + uint32_t(g.nb) * (uint32_t(iy >> 4) + uint32_t(g.nb) * uint32_t(iz >> 4));
+}
+
+__global__ void __launch_bounds__(kFewThreads) bin_count_few_kernel(const float *__restrict__ pos, int64_t N,
+                                                                    BinGeom g, int n_bricks, int64_t chunk,
+                                                                    uint32_t *__restrict__ mat, DevStatus st) {
+    __shared__ uint32_t hist[kFewBricks];
+    for (int k = threadIdx.x; k < n_bricks; k += kFewThreads) hist[k] = 0u;
+    __syncthreads();
+    const int64_t lo = int64_t(blockIdx.x) * chunk, hi = lo + chunk < N ? lo + chunk : N;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += kFewThreads) {
         float x, y, z;
         load_particle(pos, i, g, st, x, y, z);
-        int ix = cell_coord(x, g.inv_cell, g.n), iy = cell_coord(y, g.inv_cell, g.n), iz = cell_coord(z, g.inv_cell, g.n);
-        uint64_t brick = uint64_t(ix >> 4) + uint64_t(g.nb) * (uint64_t(iy >> 4) + uint64_t(g.nb) * uint64_t(iz >> 4));
-        uint32_t slot = atomicAdd(&cursor[brick], 1u);
+        atomicAdd(&hist[brick_of(x, y, z, g)], 1u);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < n_bricks; k += kFewThreads) mat[int64_t(blockIdx.x) * n_bricks + k] = hist[k];
+}
+
+// mat read in brick-major order: element (brick k, CTA c) at index k*G + c.
+struct BrickMajor {
+    const uint32_t *mat;
+    int64_t nb;
+    __device__ __forceinline__ uint32_t operator()(int64_t i) const {
+        return mat[(i % kFewGrid) * nb + i / kFewGrid];
+    }
+};
+
+__global__ void __launch_bounds__(kFewThreads) bin_scatter_few_kernel(const float *__restrict__ pos, int64_t N,
+                                                                      BinGeom g, int n_bricks, int64_t chunk,
+                                                                      const uint32_t *__restrict__ base,
+                                                                      float4 *__restrict__ tmp, DevStatus st) {
+    __shared__ uint32_t cur[kFewBricks];
+    for (int k = threadIdx.x; k < n_bricks; k += kFewThreads) cur[k] = base[int64_t(k) * kFewGrid + blockIdx.x];
+    __syncthreads();
+    const int64_t lo = int64_t(blockIdx.x) * chunk, hi = lo + chunk < N ? lo + chunk : N;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += kFewThreads) {
+        float x, y, z;
+        load_particle(pos, i, g, st, x, y, z);
+        uint32_t slot = atomicAdd(&cur[brick_of(x, y, z, g)], 1u);
         tmp[slot] = make_float4(x, y, z, __int_as_float(int(i)));
     }
 }
@@ -95,14 +170,14 @@ struct ClassReg {
 
 __global__ void __launch_bounds__(kSortThreads) brick_sort_kernel(const float4 *__restrict__ tmp,
                                                                   const uint32_t *__restrict__ brick_start,
-                                                                  int64_t n_bricks, BinGeom g,
+                                                                  int64_t bstride, int64_t n_bricks, BinGeom g,
                                                                   float4 *__restrict__ spos,
                                                                   uint32_t *__restrict__ cell_start, ClassReg cr) {
     __shared__ uint32_t hist[kBrickCells];
     __shared__ uint32_t warps[kSortThreads / 32];
     constexpr int per = kBrickCells / kSortThreads;  // 8
     for (int64_t brick = blockIdx.x; brick < n_bricks; brick += gridDim.x) {
-        uint32_t bs = brick_start[brick], be = brick_start[brick + 1];
+        uint32_t bs = brick_start[brick * bstride], be = brick_start[(brick + 1) * bstride];
         for (int k = threadIdx.x; k < kBrickCells; k += kSortThreads) hist[k] = 0;
         __syncthreads();
         for (uint32_t e = bs + threadIdx.x; e < be; e += kSortThreads) {
@@ -164,27 +239,50 @@ void launch_bin_cells(const float *pos, int64_t N, float L, int n, bool wrap, co
                       const FofBuffers &fb, const DevStatus &st, cudaStream_t s) {
     BinGeom g{L, float(double(n) / double(L)), n, bricks_per_axis(n), wrap};
     int64_t n_bricks = int64_t(g.nb) * g.nb * g.nb;
-    cudaMemsetAsync(fb.brick_count, 0, sizeof(uint32_t) * size_t(n_bricks), s);
     cudaMemsetAsync(fb.counters, 0, 2 * sizeof(uint32_t), s);
-    {
-        JFOF_TRACE("bin_count", s);
-        bin_count_kernel<<<grid_for(N, 256), 256, 0, s>>>(pos, N, g, fb.brick_count, st);
-    }
-    {
-        JFOF_TRACE("scan", s);
-        scan_exclusive(LoadU32{fb.brick_count}, n_bricks, fb.brick_start, fb.scan_tmp, s);
-    }
-    cudaMemcpyAsync(fb.cursor, fb.brick_start, sizeof(uint32_t) * size_t(n_bricks), cudaMemcpyDeviceToDevice, s);
-    {
-        JFOF_TRACE("bin_scatter", s);
-        bin_scatter_kernel<<<grid_for(N, 256), 256, 0, s>>>(pos, N, g, fb.cursor, fb.tmp, st);
+    const bool few = n_bricks <= kFewBricks;
+    const uint32_t *bstart = fb.brick_start;
+    int64_t bstride = 1;
+    if (few) {
+        const int64_t chunk = (N + kFewGrid - 1) / kFewGrid;
+        {
+            JFOF_TRACE("bin_count", s);
+            bin_count_few_kernel<<<kFewGrid, kFewThreads, 0, s>>>(pos, N, g, int(n_bricks), chunk, fb.bin_mat, st);
+        }
+        {
+            JFOF_TRACE("scan", s);
+            scan_exclusive(BrickMajor{fb.bin_mat, n_bricks}, n_bricks * kFewGrid, fb.bin_base, fb.scan_tmp, s);
+        }
+        {
+            JFOF_TRACE("bin_scatter", s);
+            bin_scatter_few_kernel<<<kFewGrid, kFewThreads, 0, s>>>(pos, N, g, int(n_bricks), chunk, fb.bin_base,
+                                                                     fb.tmp, st);
+        }
+        bstart = fb.bin_base;
+        bstride = kFewGrid;
+    } else {
+        cudaMemsetAsync(fb.brick_count, 0, sizeof(uint32_t) * size_t(n_bricks), s);
+        {
+            JFOF_TRACE("bin_count", s);
+            bin_count_kernel<<<grid_for(N, 256), 256, 0, s>>>(pos, N, g, fb.brick_count, st);
+        }
+        {
+            JFOF_TRACE("scan", s);
+            scan_exclusive(LoadU32{fb.brick_count}, n_bricks, fb.brick_start, fb.scan_tmp, s);
+        }
+        cudaMemcpyAsync(fb.cursor, fb.brick_start, sizeof(uint32_t) * size_t(n_bricks), cudaMemcpyDeviceToDevice,
+                        s);
+        {
+            JFOF_TRACE("bin_scatter", s);
+            bin_scatter_kernel<<<grid_for(N, 256), 256, 0, s>>>(pos, N, g, fb.cursor, fb.tmp, st);
+        }
     }
     ClassReg cr{lp.S, lp.T, fb.dense_id, fb.dense_cells, fb.counters, lp.D_cap, fb.medium_cells, fb.counters + 1,
                 medium_cap(N)};
     {
         JFOF_TRACE("brick_sort", s);
         brick_sort_kernel<<<grid_for(n_bricks * kSortThreads, kSortThreads, 4), kSortThreads, 0, s>>>(
-            fb.tmp, fb.brick_start, n_bricks, g, fb.spos, fb.cell_start, cr);
+            fb.tmp, bstart, bstride, n_bricks, g, fb.spos, fb.cell_start, cr);
     }
     set_u32_kernel<<<1, 1, 0, s>>>(fb.cell_start + n_bricks * kBrickCells, uint32_t(N));
 }
@@ -1174,6 +1272,14 @@ void launch_link_core(const jfof_cells &c, const FofBuffers &fb, const LinkParam
                float(double(c.L) / c.n_axis), float(gap * gap), c.n_axis, bricks_per_axis(c.n_axis), lp.k,
                lp.k * lp.k * lp.k, lp.S, lp.T, lp.D_cap};
     const float4 *spos = reinterpret_cast<const float4 *>(c.spos);
+    // Warps of the list-driven kernels (they take cells from a work counter, so
+    // any count is correct): at most one per cell the class can hold, so a
+    // small box does not launch a full grid of warps that find no work.
+    auto list_threads = [&](int64_t cap, int64_t min_particles) {
+        int64_t w = N / min_particles + 1;
+        return (w < cap ? w : cap) * 32;
+    };
+    const int64_t med_thr = list_threads(medium_cap(N), lp.S + 1), dense_thr = list_threads(lp.D_cap, lp.T + 1);
     {
         JFOF_TRACE("link_init", s);
         iota_kernel<<<grid_for(N, 256), 256, 0, s>>>(fb.parent, N);
@@ -1182,13 +1288,13 @@ void launch_link_core(const jfof_cells &c, const FofBuffers &fb, const LinkParam
     // local passes first: they write parent with plain stores, each for its own cell
     if (lp.T > 0) {
         JFOF_TRACE("dense_cells", s);
-        dense_cells_kernel<<<grid_for(lp.D_cap * 32, 32 * kDenseWarps, 8), 32 * kDenseWarps, 0, s>>>(
+        dense_cells_kernel<<<grid_for(dense_thr, 32 * kDenseWarps, 8), 32 * kDenseWarps, 0, s>>>(
             fb.spos, fb.tmp, c.cell_start, fb.dense_cells, fb.counters, fb.counters + 2, fb.sub_start, fb.sub_rows,
             fb.parent, g);
     }
     {
         JFOF_TRACE("link_medium_local", s);
-        medium_local_kernel<<<grid_for(medium_cap(N) * 32, 32 * kMedWarps, 8), 32 * kMedWarps, 0, s>>>(
+        medium_local_kernel<<<grid_for(med_thr, 32 * kMedWarps, 8), 32 * kMedWarps, 0, s>>>(
             spos, c.cell_start, fb.medium_cells, fb.counters + 1, fb.counters + 3, medium_cap(N), g, fb.parent, st);
     }
     // then everything that unites across cells (atomic hooks only)
@@ -1198,13 +1304,13 @@ void launch_link_core(const jfof_cells &c, const FofBuffers &fb, const LinkParam
     }
     {
         JFOF_TRACE("link_medium", s);
-        medium_kernel<<<grid_for(medium_cap(N) * 32, 32 * kMedXWarps, 8), 32 * kMedXWarps, 0, s>>>(
+        medium_kernel<<<grid_for(med_thr, 32 * kMedXWarps, 8), 32 * kMedXWarps, 0, s>>>(
             spos, c.cell_start, fb.medium_cells, fb.counters + 1, fb.counters + 4, fb.dense_id, medium_cap(N), g,
             fb.parent, st);
     }
     if (lp.T > 0) {
         JFOF_TRACE("link_dense_nbr", s);
-        dense_nbr_kernel<<<grid_for(lp.D_cap * 32, 32 * kNbrWarps, 8), 32 * kNbrWarps, 0, s>>>(
+        dense_nbr_kernel<<<grid_for(dense_thr, 32 * kNbrWarps, 8), 32 * kNbrWarps, 0, s>>>(
             spos, c.cell_start, fb.dense_cells, fb.counters, fb.counters + 5, fb.dense_id, fb.sub_start, fb.sub_rows,
             g, fb.parent, st);
     }

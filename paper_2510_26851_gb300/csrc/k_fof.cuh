@@ -15,6 +15,10 @@ constexpr int kDefaultDenseThreshold = 64;
 constexpr int kDefaultSmallThreshold = 8;
 // Output-order buckets of the label scatter (at most this many).
 constexpr int kTailBuckets = 256;
+// Binning of grids with at most kFewBricks bricks: a counting sort by
+// kFewGrid CTAs over contiguous chunks (no global atomics).
+constexpr int kFewBricks = 4096;
+constexpr int kFewGrid = 2 * kNumSMs;
 
 // One IEEE binary32 multiply on the host (b*b for the link threshold).
 inline float host_mul(float a, float b) {
@@ -42,6 +46,8 @@ struct FofBuffers {
     uint16_t *sub_rows;    // [D_cap][kSubSide^2] bit x of row (y, z): sub-cell non-empty
     uint32_t *medium_cells;// [medium_cap]
     uint32_t *bucket_fill; // [kTailBuckets] label-scatter bucket cursors
+    uint32_t *bin_mat;     // [kFewGrid][bricks] per-CTA brick counts (few-brick grids)
+    uint32_t *bin_base;    // [bricks * kFewGrid + 1] their brick-major exclusive scan
 };
 
 // Dense-path parameters derived on the host from (N, L, b, n, T).

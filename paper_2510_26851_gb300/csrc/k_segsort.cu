@@ -233,7 +233,7 @@ void launch_segsort(const uint32_t *off, int64_t S, int32_t *data, int64_t cap, 
     JFOF_TRACE("segsort", s);
     int64_t list_cap = list_words - 1;
     cudaMemsetAsync(list, 0, sizeof(uint32_t), s);
-    segsort_warp_kernel<<<grid_for(S * 32, 32 * kSegWarps, 8), 32 * kSegWarps, 0, s>>>(off, S, S_dev, cap, data,
+    segsort_warp_kernel<<<grid_for(S * 8, 32 * kSegWarps, 8), 32 * kSegWarps, 0, s>>>(off, S, S_dev, cap, data,
                                                                                        list, list_cap);
     segsort_block_kernel<<<grid_for(list_cap * kSegBlock, kSegBlock, 4), kSegBlock, 0, s>>>(off, data, list,
                                                                                            list_cap);
