@@ -14,7 +14,7 @@ constexpr uint32_t kDenseMaxM = 65535;
 constexpr int kDefaultDenseThreshold = 64;
 constexpr int kDefaultSmallThreshold = 8;
 // Output-order buckets of the label scatter (at most this many).
-constexpr int kTailBuckets = 256;
+constexpr int kTailBuckets = 1024;
 // Binning of grids with at most kFewBricks bricks: a counting sort by
 // kFewGrid CTAs over contiguous chunks (no global atomics).
 constexpr int kFewBricks = 4096;

@@ -25,7 +25,8 @@ namespace jfof {
 constexpr int kTailThreads = 256;
 constexpr int kTailItems = 16;
 constexpr int kTailTile = kTailThreads * kTailItems;
-static_assert(kTailBuckets == kTailThreads, "one bucket counter per thread");
+constexpr int kTailBPT = kTailBuckets / kTailThreads;  // bucket counters per thread
+static_assert(kTailBuckets % kTailThreads == 0, "bucket counters split evenly over the threads");
 
 namespace {
 
@@ -118,7 +119,8 @@ __global__ void __launch_bounds__(kTailThreads) tail_partition_kernel(
     __shared__ uint2 stage[kTailTile];
     const int tid = threadIdx.x, lane = tid & 31;
     const int64_t tile0 = int64_t(blockIdx.x) * kTailTile;
-    hist[tid] = 0u;
+#pragma unroll
+    for (int j = 0; j < kTailBPT; ++j) hist[tid * kTailBPT + j] = 0u;
     __syncthreads();
     uint32_t key[kTailItems], val[kTailItems], rank[kTailItems];
 #pragma unroll
@@ -151,9 +153,20 @@ __global__ void __launch_bounds__(kTailThreads) tail_partition_kernel(
         rank[k] = ok ? atomicAdd(&hist[uint32_t(orig) >> shift], 1u) : 0u;
     }
     __syncthreads();
-    uint32_t c = hist[tid], total;
-    lstart[tid] = block_exclusive_scan(c, warp_sums, &total);
-    gbase[tid] = c ? atomicAdd(&bucket_fill[tid], c) : 0u;
+    uint32_t c[kTailBPT], sum = 0u, total;
+#pragma unroll
+    for (int j = 0; j < kTailBPT; ++j) {
+        c[j] = hist[tid * kTailBPT + j];
+        sum += c[j];
+    }
+    uint32_t pre = block_exclusive_scan(sum, warp_sums, &total);
+#pragma unroll
+    for (int j = 0; j < kTailBPT; ++j) {
+        const int b = tid * kTailBPT + j;
+        lstart[b] = pre;
+        gbase[b] = c[j] ? atomicAdd(&bucket_fill[b], c[j]) : 0u;
+        pre += c[j];
+    }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < kTailItems; ++k)
