@@ -449,13 +449,14 @@ __device__ __forceinline__ void lunite(int *lp, int a, int b) {
 
 // ---------------------------------------------------------------------------
 // Medium cells, local part: one warp per cell.  The cell's particles are
-// staged in shared memory and all their pairs tested in 32-wide tiles
-// (lane = one particle, the other broadcast), joined by a shared-memory
-// union-find over local indices; then parent[slot] = first slot of the
-// slot's local component.  A cell larger than the staging area (possible only
-// when it cannot take the dense path) links its own pairs through the global
-// forest instead.  Runs before any kernel that unites across cells, since it
-// writes parent with plain stores.
+// staged in shared memory and all their pairs tested (lane = one particle,
+// the other broadcast).  Up to 64 particles: adjacency bitmasks and a
+// breadth-first search over them; larger cells: a shared-memory union-find
+// over local indices.  Then parent[slot] = first slot of the slot's local
+// component.  A cell larger than the staging area (possible only when it
+// cannot take the dense path) links its own pairs through the global forest
+// instead.  Runs before any kernel that unites across cells, since it writes
+// parent with plain stores.
 constexpr int kMedWarps = 4;
 constexpr int kMedCap = 256;
 
@@ -490,33 +491,36 @@ __global__ void __launch_bounds__(32 * kMedWarps) medium_local_kernel(const floa
         }
         __syncwarp();
         if (mA <= 32) {
-            // one particle per lane: 32-bit adjacency masks, same closure
+            // One particle per lane: its 32-bit adjacency mask (every pair
+            // tested with the exact predicate).  Components by breadth-first
+            // search from the lowest unvisited particle: a frontier step is one
+            // warp OR-reduction of the frontier's rows, and the seed is the
+            // component's smallest local index.
             const bool h0 = lane < mA;
             float4 q0 = h0 ? sp[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
             unsigned r0 = h0 ? 1u << lane : 0u;
             for (int i = 0; i < mA; ++i)
                 if (h0 && linked(sp[i], q0, g)) r0 |= 1u << i;
-            for (int round = 0; round < 6; ++round) {
-                unsigned n0 = r0;
-                for (int i = 0; i < mA; ++i) {
-                    unsigned ri = __shfl_sync(0xffffffffu, r0, i);
-                    if ((r0 >> i) & 1u) n0 |= ri;
+            unsigned unvisited = mA == 32 ? 0xffffffffu : (1u << mA) - 1u;
+            int root = 0;
+            while (unvisited) {
+                const int seed = __ffs(int(unvisited)) - 1;
+                unsigned comp = 1u << seed, frontier = comp;
+                while (frontier) {
+                    unsigned nb = __reduce_or_sync(0xffffffffu, ((frontier >> lane) & 1u) ? r0 : 0u);
+                    frontier = nb & ~comp;
+                    comp |= nb;
                 }
-                bool changed = n0 != r0;
-                r0 = n0;
-                if (!__any_sync(0xffffffffu, changed)) break;
+                if ((comp >> lane) & 1u) root = seed;
+                unvisited &= ~comp;
             }
-            if (h0) parent[a0 + lane] = int(a0) + __ffs(int(r0)) - 1;
+            if (h0) parent[a0 + lane] = int(a0) + root;
             __syncwarp();
             continue;
         }
         if (mA <= 64) {
-            // Warp-synchronous components for up to 64 particles: each lane owns
-            // particles lane and lane+32 and builds their 64-bit adjacency masks
-            // (every pair tested with the exact predicate), then the reach sets
-            // are closed under r_j |= r_i for i in r_j (each round doubles the
-            // path length covered) until no mask changes.  The component's
-            // smallest local index is the lowest set bit.
+            // The same for up to 64 particles: each lane owns particles lane
+            // and lane+32 and their 64-bit adjacency masks.
             const bool h0 = lane < mA, h1 = lane + 32 < mA;
             float4 q0 = h0 ? sp[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
             float4 q1 = h1 ? sp[lane + 32] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -526,20 +530,26 @@ __global__ void __launch_bounds__(32 * kMedWarps) medium_local_kernel(const floa
                 if (h0 && linked(pi, q0, g)) r0 |= 1ull << i;
                 if (h1 && linked(pi, q1, g)) r1 |= 1ull << i;
             }
-            for (int round = 0; round < 8; ++round) {
-                unsigned long long n0 = r0, n1 = r1;
-                for (int i = 0; i < mA; ++i) {
-                    unsigned long long ri = __shfl_sync(0xffffffffu, i < 32 ? r0 : r1, i & 31);
-                    if ((r0 >> i) & 1ull) n0 |= ri;
-                    if ((r1 >> i) & 1ull) n1 |= ri;
+            unsigned long long unvisited = mA == 64 ? ~0ull : (1ull << mA) - 1ull;
+            int root0 = 0, root1 = 0;
+            while (unvisited) {
+                const int seed = __ffsll((long long)unvisited) - 1;
+                unsigned long long comp = 1ull << seed, frontier = comp;
+                while (frontier) {
+                    unsigned long long v = (((frontier >> lane) & 1ull) ? r0 : 0ull) |
+                                           (((frontier >> (lane + 32)) & 1ull) ? r1 : 0ull);
+                    unsigned lo = __reduce_or_sync(0xffffffffu, unsigned(v));
+                    unsigned hi = __reduce_or_sync(0xffffffffu, unsigned(v >> 32));
+                    unsigned long long nb = (static_cast<unsigned long long>(hi) << 32) | lo;
+                    frontier = nb & ~comp;
+                    comp |= nb;
                 }
-                bool changed = n0 != r0 || n1 != r1;
-                r0 = n0;
-                r1 = n1;
-                if (!__any_sync(0xffffffffu, changed)) break;
+                if ((comp >> lane) & 1ull) root0 = seed;
+                if ((comp >> (lane + 32)) & 1ull) root1 = seed;
+                unvisited &= ~comp;
             }
-            if (h0) parent[a0 + lane] = int(a0) + __ffsll((long long)r0) - 1;
-            if (h1) parent[a0 + lane + 32] = int(a0) + __ffsll((long long)r1) - 1;
+            if (h0) parent[a0 + lane] = int(a0) + root0;
+            if (h1) parent[a0 + lane + 32] = int(a0) + root1;
             __syncwarp();
             continue;
         }
