@@ -62,6 +62,39 @@ ALGO_BYTES = {
 LINK_PARTS = ("dense_cells", "link_medium_local", "link_small", "link_medium", "link_dense_nbr")
 
 
+# DRAM traffic of the link step per launch (ncu, dram__bytes_read.sum +
+# dram__bytes_write.sum over its five launches), committed with the digest of
+# the kernel sources it was taken on: it is reported only while those sources
+# are unchanged, else null.
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_link_1024cubed.md")
+
+
+def kernel_sources_digest():
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2510_26851_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(f.encode())
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()
+
+
+def link_traffic():
+    import re
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            txt = fh.read()
+    except OSError:
+        return None
+    dig = re.search(r"kernel sources sha256: ([0-9a-f]{64})", txt)
+    byt = re.search(r"link DRAM bytes per launch: ([0-9]+)", txt)
+    if not dig or not byt or dig.group(1) != kernel_sources_digest():
+        return None
+    return int(byt.group(1))
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -327,8 +360,9 @@ def main():
         nb = -(-n_axis // 16)
         algo_bytes += 4 * nb ** 3 * 4096
     achieved = algo_bytes / (per_launch_ms * 1e-3) / 1e9
+    traffic = link_traffic() if (name == "link" and args.workload == "1024") else None
     roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": algo_bytes, "launch_ms": per_launch_ms}
     kernels = {k: {"launches": c, "ms_per_step": t / args.steps} for k, (c, t) in trace.items()}
 
