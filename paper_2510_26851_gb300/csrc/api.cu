@@ -92,7 +92,8 @@ size_t fof_layout(int64_t N, int n, FofBuffers *fb, void *base) {
     f.dense_id = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * size_t(cell_table_entries(n))));
     int64_t D_cap = dense_cap(N);
     f.dense_cells = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * size_t(D_cap)));
-    f.counters = reinterpret_cast<uint32_t *>(take(6 * sizeof(uint32_t)));
+    f.counters = reinterpret_cast<uint32_t *>(take(kCounters * sizeof(uint32_t)));
+    f.small_slots = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * size_t(N)));
     f.sub_start = reinterpret_cast<uint16_t *>(take(sizeof(uint16_t) * size_t(D_cap) * (kSubMax + 1)));
     f.sub_rows = reinterpret_cast<uint16_t *>(take(sizeof(uint16_t) * size_t(D_cap) * (kSubSide * kSubSide)));
     f.medium_cells = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * size_t(medium_cap(N))));

@@ -166,6 +166,8 @@ struct ClassReg {
     uint32_t *medium_cells;   // [M_cap]
     uint32_t *nmedium;        // counter
     int64_t M_cap;
+    uint32_t *small_slots;    // [N] slots of the particles of small cells (null: no list)
+    uint32_t *nsmall;         // counter
 };
 
 __global__ void __launch_bounds__(kSortThreads) brick_sort_kernel(const float4 *__restrict__ tmp,
@@ -175,6 +177,7 @@ __global__ void __launch_bounds__(kSortThreads) brick_sort_kernel(const float4 *
                                                                   uint32_t *__restrict__ cell_start, ClassReg cr) {
     __shared__ uint32_t hist[kBrickCells];
     __shared__ uint32_t warps[kSortThreads / 32];
+    __shared__ uint32_t small_base;
     constexpr int per = kBrickCells / kSortThreads;  // 8
     for (int64_t brick = blockIdx.x; brick < n_bricks; brick += gridDim.x) {
         uint32_t bs = brick_start[brick * bstride], be = brick_start[(brick + 1) * bstride];
@@ -220,6 +223,24 @@ __global__ void __launch_bounds__(kSortThreads) brick_sort_kernel(const float4 *
                 }
             }
         }
+        if (cr.small_slots) {
+            // slots of the small cells' particles, appended in cell order
+            uint32_t ns = 0;
+#pragma unroll
+            for (int k = 0; k < per; ++k)
+                if (v[k] <= uint32_t(cr.S)) ns += v[k];
+            uint32_t ntot;
+            uint32_t so = block_exclusive_scan(ns, warps, &ntot);
+            if (threadIdx.x == 0) small_base = ntot ? atomicAdd(cr.nsmall, ntot) : 0u;
+            __syncthreads();
+            uint32_t w = small_base + so, cs = bs + pre - s;  // pre has advanced past this thread's cells
+#pragma unroll
+            for (int k = 0; k < per; ++k) {
+                if (v[k] <= uint32_t(cr.S))
+                    for (uint32_t q = 0; q < v[k]; ++q) cr.small_slots[w++] = cs + q;
+                cs += v[k];
+            }
+        }
         __syncthreads();
         for (uint32_t e = bs + threadIdx.x; e < be; e += kSortThreads) {
             float4 q = tmp[e];
@@ -239,7 +260,7 @@ void launch_bin_cells(const float *pos, int64_t N, float L, int n, bool wrap, co
                       const FofBuffers &fb, const DevStatus &st, cudaStream_t s) {
     BinGeom g{L, float(double(n) / double(L)), n, bricks_per_axis(n), wrap};
     int64_t n_bricks = int64_t(g.nb) * g.nb * g.nb;
-    cudaMemsetAsync(fb.counters, 0, 2 * sizeof(uint32_t), s);
+    cudaMemsetAsync(fb.counters, 0, kCounters * sizeof(uint32_t), s);
     const bool few = n_bricks <= kFewBricks;
     const uint32_t *bstart = fb.brick_start;
     int64_t bstride = 1;
@@ -278,7 +299,7 @@ void launch_bin_cells(const float *pos, int64_t N, float L, int n, bool wrap, co
         }
     }
     ClassReg cr{lp.S, lp.T, fb.dense_id, fb.dense_cells, fb.counters, lp.D_cap, fb.medium_cells, fb.counters + 1,
-                medium_cap(N)};
+                medium_cap(N), lp.S < INT32_MAX ? fb.small_slots : nullptr, fb.counters + 6};
     {
         JFOF_TRACE("brick_sort", s);
         brick_sort_kernel<<<grid_for(n_bricks * kSortThreads, kSortThreads, 4), kSortThreads, 0, s>>>(
@@ -366,7 +387,8 @@ __global__ void iota_kernel(int *__restrict__ p, int64_t N) {
 }
 
 // ---------------------------------------------------------------------------
-// Small cells: one thread per particle.  Pairs with later particles of its
+// Small cells: one thread per particle of a small cell (the list written by
+// the brick sort, in cell order).  Pairs with later particles of its
 // cell and with every particle of a small forward neighbour cell that lies
 // within reach (the particle's gap to that cell <= 1.02 b).  The 13 forward
 // offsets are compile-time constants here (packed 2 bits per offset and
@@ -377,9 +399,17 @@ constexpr uint32_t kFwdX = 0x2492492u, kFwdY = 0x2a540a9u, kFwdZ = 0x2aaaa55u;
 __device__ __forceinline__ int fwd_comp(uint32_t packed, int o) { return int((packed >> (2 * o)) & 3u) - 1; }
 
 __global__ void __launch_bounds__(256) small_kernel(const float4 *__restrict__ spos,
-                                                    const uint32_t *__restrict__ cell_start, int64_t N, LinkGeom g,
+                                                    const uint32_t *__restrict__ cell_start,
+                                                    const uint32_t *__restrict__ small_slots,
+                                                    const uint32_t *__restrict__ nsmall, uint32_t *next, LinkGeom g,
                                                     int *parent, DevStatus st) {
-    for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < N; s += int64_t(gridDim.x) * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t ns = *nsmall;
+    // a warp takes 32 consecutive entries of the list of small-cell particles
+    for (int64_t c = next_task(next, lane); c * 32 < ns; c = next_task(next, lane)) {
+        const int64_t t = c * 32 + lane;
+        if (t >= ns) continue;
+        const int64_t s = small_slots[t];
         float4 p = spos[s];
         int cx = cell_coord(p.x, g.inv_cell, g.n), cy = cell_coord(p.y, g.inv_cell, g.n),
             cz = cell_coord(p.z, g.inv_cell, g.n);
@@ -1295,6 +1325,7 @@ void launch_link_core(const jfof_cells &c, const FofBuffers &fb, const LinkParam
         iota_kernel<<<grid_for(N, 256), 256, 0, s>>>(fb.parent, N);
     }
     cudaMemsetAsync(fb.counters + 2, 0, 4 * sizeof(uint32_t), s);  // work counters
+    cudaMemsetAsync(fb.counters + 7, 0, sizeof(uint32_t), s);
     // local passes first: they write parent with plain stores, each for its own cell
     if (lp.T > 0) {
         JFOF_TRACE("dense_cells", s);
@@ -1310,7 +1341,8 @@ void launch_link_core(const jfof_cells &c, const FofBuffers &fb, const LinkParam
     // then everything that unites across cells (atomic hooks only)
     if (lp.S > 0) {
         JFOF_TRACE("link_small", s);
-        small_kernel<<<grid_full(N, 256), 256, 0, s>>>(spos, c.cell_start, N, g, fb.parent, st);
+        small_kernel<<<grid_for(N, 256, 8), 256, 0, s>>>(spos, c.cell_start, fb.small_slots, fb.counters + 6,
+                                                          fb.counters + 7, g, fb.parent, st);
     }
     {
         JFOF_TRACE("link_medium", s);

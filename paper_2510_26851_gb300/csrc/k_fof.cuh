@@ -13,6 +13,7 @@ constexpr int kSubMax = kSubSide * kSubSide * kSubSide;  // 729
 constexpr uint32_t kDenseMaxM = 65535;
 constexpr int kDefaultDenseThreshold = 64;
 constexpr int kDefaultSmallThreshold = 8;
+constexpr int kCounters = 8;
 // Output-order buckets of the label scatter (at most this many).
 constexpr int kTailBuckets = 1024;
 // Binning of grids with at most kFewBricks bricks: a counting sort by
@@ -41,7 +42,9 @@ struct FofBuffers {
     int *parent;           // [N]
     uint32_t *dense_id;    // [cell table]
     uint32_t *dense_cells; // [D_cap]
-    uint32_t *counters;    // [6]: dense cells, medium cells, four work counters
+    uint32_t *counters;    // [kCounters]: dense cells, medium cells, four work counters,
+                           // small-cell particles, small work counter
+    uint32_t *small_slots; // [N] slots of the particles of small cells
     uint16_t *sub_start;   // [D_cap][kSubMax + 1]
     uint16_t *sub_rows;    // [D_cap][kSubSide^2] bit x of row (y, z): sub-cell non-empty
     uint32_t *medium_cells;// [medium_cap]

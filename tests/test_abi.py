@@ -56,3 +56,39 @@ def test_host_side_argument_checks(lib):
     assert lib.jfof_fof_bytes(1000, 8, ctypes.byref(sz)) == 0 and sz.value > 32 * 1000
     lib.jfof_strerror.restype = ctypes.c_char_p
     assert b"workspace" in lib.jfof_strerror(3)
+
+
+def _dense_ok(N, L, b, n):
+    # the host's rule for the sub-cell path of dense cells (k <= 9 sub-cells of
+    # side s/k with sqrt(3)(s/k + 2 eps) <= b (1 - 1e-4) and b + 2 eps < 2 s/k)
+    import math
+    s = L / n
+    k = max(1, math.ceil(s * math.sqrt(3.0) * 1.02 / b))
+    sf = s / k
+    eps = 4.0 * L * 2.0 ** -24
+    return (n >= 5 and k <= 9 and math.sqrt(3.0) * (sf + 2 * eps) <= b * (1 - 1e-4)
+            and (b + 2 * eps) / sf < 2.0)
+
+
+def test_default_grid_keeps_the_dense_path(lib):
+    # the default grid is the largest legal n with n^3 <= N, raised (by at most
+    # max(2, n/8)) to the first n whose cells are narrow enough for 9 sub-cells
+    import synth
+    n = ctypes.c_int32()
+    lib.jfof_default_cells_per_axis.argtypes = [ctypes.c_int64, ctypes.c_float, ctypes.c_float,
+                                                ctypes.POINTER(ctypes.c_int32)]
+    raised = 0
+    for N, L in [(73228, 129.0), (32876, 395.0), (243739, 338.0), (1203185, 220.0), (6417007, 318.0),
+                 (32 ** 3, 100.0), (40 ** 3 + 1000, 75.0), (150_000, 50.0), (1 << 24, 250.0)]:
+        b = synth.linking_length(L, N)
+        assert lib.jfof_default_cells_per_axis(N, L, b, ctypes.byref(n)) == 0
+        n0 = 3
+        while (n0 + 1) ** 3 <= N:
+            n0 += 1
+        cands = [m for m in range(n0, n0 + max(2, n0 // 8) + 1) if _dense_ok(N, L, b, m)]
+        if cands:
+            assert n.value == cands[0], (N, L, n.value, cands)
+            raised += n.value > n0
+        else:
+            assert n.value == n0
+    assert raised >= 1  # 73228 particles in L = 129: n = 41 has k = 10, so 42

@@ -86,6 +86,22 @@ def test_labels_invariant_across_grids(J, seed):
         assert np.array_equal(r.label.cpu().numpy(), lab_ref), n
 
 
+def test_both_binning_paths(J):
+    # grids of at most 4096 bricks (16^3 cells each) bin with the per-CTA
+    # counting sort, larger ones with brick cursors: n = 256 and n = 257 sit on
+    # either side of that switch; the default and the largest grid as well
+    spec = synth.BoxSpec("t", 300_000, 100.0, synth.linking_length(100.0, 300_000), 1500, 0.55, 11)
+    pos, _ = synth.generate(spec, device="cuda", velocities=False)
+    pos_np = pos.cpu().numpy()
+    lab_ref = oracle.fof_labels(pos_np, spec.L, spec.b)
+    nmax = J.max_cells_per_axis(spec.L, spec.b)
+    assert nmax > 257
+    for n in (0, 256, 257, nmax):
+        _, r, H = run_fof(J, pos_np, spec.L, spec.b, spec.min_size, n_axis=n)
+        assert np.array_equal(r.label.cpu().numpy(), lab_ref), n
+        check_groups(r, H, lab_ref, spec.min_size)
+
+
 @pytest.mark.parametrize("boost", [1.0, 2.5])
 def test_labels_invariant_across_cell_classes(J, boost):
     # dense threshold 0 turns the sub-cell path off; 1 sends almost every cell
