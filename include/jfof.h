@@ -310,6 +310,26 @@ int jfof_fof(jfof_ctx *ctx, const float *pos, int64_t N, float L, float b, int32
              int32_t *halo_id, int32_t *count, int32_t *halo_start, int32_t *members,
              int32_t *n_halos);
 
+/* One step of the whole plain path (Sec. 2 steps (i)-(vi) and Sec. 3.1,
+   Eq. 4: a1-a8) from HOST buffers.  h_pos / h_vel: host float32 [N,3]
+   (h_vel may be NULL: no velocity outputs); page-locked memory (cudaHostAlloc
+   or cudaHostRegister) lets the uploads run asynchronously, pageable memory
+   works but the copies then block the caller.  d_pos / d_vel: the caller's
+   device staging buffers [N,3] (d_vel NULL iff h_vel is NULL); they receive
+   the uploaded inputs and stay valid afterwards.  Positions are uploaded on
+   the context's stream; velocities on a library-owned copy stream after the
+   positions, so their upload overlaps the FoF kernels; the halo properties
+   and everything later enqueued on the context's stream wait for it.  Then
+   exactly jfof_fof (ws of jfof_fof_all_bytes(N, n) bytes) and
+   jfof_halo_props with H_cap = max(1, N / min_size), with the same outputs
+   and the same errors; host buffers must stay unchanged until the context's
+   stream has passed this call.  Argument errors return before any copy. */
+int jfof_fof_host(jfof_ctx *ctx, const float *h_pos, const float *h_vel, int64_t N, float L, float b,
+                  int32_t n_axis, uint32_t flags, int32_t min_size, float particle_mass, float *d_pos,
+                  float *d_vel, void *ws, size_t ws_bytes, int32_t *label, int32_t *halo_id,
+                  int32_t *count, int32_t *halo_start, int32_t *members, int32_t *n_halos,
+                  float *mass, float *com, float *vmean, float *sigv);
+
 /* ---------------------------------------------------------------------- */
 /* No-allocation variant (the paper has no counterpart).                   */
 

@@ -31,7 +31,7 @@ EXPORTED = [
     "jfof_prob_coef", "jfof_pairs_bytes", "jfof_pairs", "jfof_reinforce_sample_bytes",
     "jfof_reinforce_sample", "jfof_reinforce_grad_bytes", "jfof_reinforce_grad", "jfof_eval_exp",
     "jfof_eval_edge_uniform", "jfof_batch_bytes", "jfof_fof_batched", "jfof_autotune",
-    "jfof_fof_static",
+    "jfof_fof_static", "jfof_fof_host",
 ]
 
 
@@ -95,6 +95,8 @@ def _declare(lib):
         "jfof_autotune": [vp, vp, i64, f32, f32, u32, i32, vp, sz, vp, vp, vp, i32, P(i32), P(i32),
                           P(i32), P(f32)],
         "jfof_fof_static": [vp, vp, i64, f32, f32, i32, u32, i32, vp, vp, vp, vp, vp, vp],
+        "jfof_fof_host": [vp, vp, vp, i64, f32, f32, i32, u32, i32, f32, vp, vp, vp, sz, vp, vp, vp, vp, vp,
+                          vp, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -351,6 +353,47 @@ def halo_props(pos: torch.Tensor, vel: torch.Tensor | None, L: float, g: Groups,
                                      _ptr(out.com), _ptr(out.vmean), _ptr(out.sigv)),
            "jfof_halo_props")
     return out
+
+
+def fof_host(h_pos: torch.Tensor, h_vel: torch.Tensor | None, L: float, b: float, min_size: int = 20,
+             n_axis: int = 0, wrap: bool = False, particle_mass: float = 1.0, device=None,
+             d_pos: torch.Tensor | None = None, d_vel: torch.Tensor | None = None,
+             workspace: torch.Tensor | None = None, out: FofResult | None = None,
+             props_out: Props | None = None):
+    """a1-a8 from host tensors (page-locked for asynchronous uploads): the
+    positions are uploaded, the velocity upload overlaps the FoF kernels, then
+    labels, groups and halo properties as ``fof`` + ``halo_props``.  Returns
+    (FofResult, Props, d_pos, d_vel); pass them back to reuse the buffers."""
+    if h_pos.device.type != "cpu" or (h_vel is not None and h_vel.device.type != "cpu"):
+        raise ValueError("fof_host takes host tensors")
+    if h_pos.dtype != torch.float32 or not h_pos.is_contiguous() or h_pos.dim() != 2 or h_pos.shape[1] != 3:
+        raise ValueError("h_pos must be contiguous float32 [N, 3]")
+    if h_vel is not None and (h_vel.dtype != torch.float32 or not h_vel.is_contiguous()
+                              or tuple(h_vel.shape) != tuple(h_pos.shape)):
+        raise ValueError("h_vel must be contiguous float32 [N, 3]")
+    dev = torch.device(device if device is not None else "cuda")
+    N = h_pos.shape[0]
+    n = default_cells_per_axis(N, L, b) if n_axis == 0 else int(n_axis)
+    if d_pos is None:
+        d_pos = torch.empty(N, 3, dtype=torch.float32, device=dev)
+    if h_vel is not None and d_vel is None:
+        d_vel = torch.empty(N, 3, dtype=torch.float32, device=dev)
+    ws = workspace if workspace is not None else _ws(fof_all_bytes(N, n), dev)
+    if out is not None:
+        label, g = out.label, out.groups
+    else:
+        label = torch.empty(N, dtype=torch.int32, device=dev)
+        g = _alloc_groups(N, min_size, dev)
+    H = g.H_cap
+    p = props_out if props_out is not None else Props(
+        torch.zeros(H, device=dev), torch.zeros(H, 3, device=dev), torch.zeros(H, 3, device=dev),
+        torch.zeros(H, device=dev))
+    _check(library().jfof_fof_host(
+        context(dev), _ptr(h_pos), _ptr(h_vel), N, L, b, n, JFOF_WRAP if wrap else 0, min_size,
+        particle_mass, _ptr(d_pos), _ptr(d_vel if h_vel is not None else None), _ptr(ws), ws.numel(),
+        _ptr(label), _ptr(g.halo_id), _ptr(g.count), _ptr(g.halo_start), _ptr(g.members),
+        _ptr(g.n_halos_dev), _ptr(p.mass), _ptr(p.com), _ptr(p.vmean), _ptr(p.sigv)), "jfof_fof_host")
+    return FofResult(label, g, n), p, d_pos, d_vel
 
 
 def halo_props_backward(vel, g: Groups, vmean, sigv, g_com=None, g_vmean=None, g_sigv=None):

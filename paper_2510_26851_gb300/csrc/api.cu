@@ -131,6 +131,9 @@ int jfof_create(jfof_ctx **ctx, int device, void *stream) {
     c->loop_budget = kDefaultLoopBudget;
     c->dense_threshold = kDefaultDenseThreshold;
     c->small_threshold = kDefaultSmallThreshold;
+    c->copy_stream = nullptr;
+    c->ev_pos = nullptr;
+    c->ev_vel = nullptr;
     if (cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess) {
         delete c;
         return JFOF_ECUDA;
@@ -157,6 +160,12 @@ int jfof_destroy(jfof_ctx *ctx) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     destroy_batch_cache(ctx->batch);
+    if (ctx->copy_stream) {
+        cudaStreamSynchronize(ctx->copy_stream);
+        cudaEventDestroy(ctx->ev_pos);
+        cudaEventDestroy(ctx->ev_vel);
+        cudaStreamDestroy(ctx->copy_stream);
+    }
     cudaFree(ctx->d_status);
     cudaFreeHost(ctx->h_status);
     delete ctx;

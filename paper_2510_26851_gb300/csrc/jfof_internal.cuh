@@ -279,6 +279,8 @@ struct jfof_ctx {
     int64_t loop_budget;
     int dense_threshold;
     int small_threshold;
+    cudaStream_t copy_stream;  // velocity uploads of jfof_fof_host (created on first use)
+    cudaEvent_t ev_pos, ev_vel;
     jfof::DevStatus dev() const { return jfof::DevStatus{d_status, loop_budget}; }
 };
 

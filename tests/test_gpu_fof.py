@@ -292,3 +292,33 @@ def test_box_256cubed_full_parity(J):
     assert np.array_equal(r.label.cpu().numpy(), lab_ref)
     check_groups(r, H, lab_ref, spec.min_size)
     props_check(J, pos, vel, r, H, spec.L, lab_ref, spec.min_size)
+
+
+def test_host_buffer_step_matches_device_path(J):
+    # jfof_fof_host (host inputs, velocity upload overlapped with the FoF
+    # kernels) gives exactly jfof_fof + jfof_halo_props; page-locked and
+    # pageable inputs, with and without velocities
+    spec = synth.BoxSpec("t", 200_000, 60.0, synth.linking_length(60.0, 200_000), 1000, 0.6, 13)
+    pos, vel = synth.generate(spec, device="cuda")
+    r = J.fof(pos, spec.L, spec.b, spec.min_size)
+    p = J.halo_props(pos, vel, spec.L, r.groups)
+    J.sync()
+    H = r.groups.n_halos
+    M = int(r.groups.halo_start[H].item())  # members past M are unused
+    for pinned in (True, False):
+        hp, hv = pos.cpu(), vel.cpu()
+        if pinned:
+            hp, hv = hp.pin_memory(), hv.pin_memory()
+        r2, p2, dp, dv = J.fof_host(hp, hv, spec.L, spec.b, spec.min_size)
+        J.sync()
+        assert torch.equal(dp, pos) and torch.equal(dv, vel)
+        assert r2.groups.n_halos == H
+        assert torch.equal(r2.label, r.label) and torch.equal(r2.groups.halo_id, r.groups.halo_id)
+        assert torch.equal(r2.groups.halo_start[:H + 1], r.groups.halo_start[:H + 1])
+        assert torch.equal(r2.groups.members[:M], r.groups.members[:M])
+        for a, b in ((p2.mass, p.mass), (p2.com, p.com), (p2.vmean, p.vmean), (p2.sigv, p.sigv)):
+            assert torch.equal(a[:H], b[:H])
+    r3, p3, _, dv3 = J.fof_host(pos.cpu().pin_memory(), None, spec.L, spec.b, spec.min_size)
+    J.sync()
+    assert dv3 is None and torch.equal(r3.label, r.label)
+    assert torch.equal(p3.com[:H], p.com[:H]) and torch.equal(p3.mass[:H], p.mass[:H])
