@@ -3,10 +3,10 @@
 // Every segment runs the same ascending-only bitonic network ("flip" step,
 // then halving steps) on P = next power of two >= m elements, the positions
 // past m behaving as +inf.  Where the network runs depends on m:
-//   m <= 1024          one warp, the segment in registers (R = P/32 values a
+//   m <= 256           one warp, the segment in registers (R = P/32 values a
 //                      lane, element t = r*32 + lane): steps whose partner is
 //                      in another lane use shuffles, the others swap registers
-//   m  > 1024          listed by the warp kernel, then one block per segment:
+//   m  > 256           listed by the warp kernel, then one block per segment:
 //                      in shared memory when P <= kSegSmem, otherwise chunks of
 //                      kSegSmem sorted in shared memory and the long steps in
 //                      global memory
@@ -19,7 +19,7 @@
 namespace jfof {
 
 constexpr int kSegWarps = 8;
-constexpr int kSegRegMax = 1024;
+constexpr int kSegRegMax = 256;
 constexpr int kSegBlock = 256;
 constexpr int kSegSmem = 8192;
 constexpr int kSegLogSmem = 13;
@@ -135,12 +135,8 @@ __global__ void __launch_bounds__(32 * kSegWarps) segsort_warp_kernel(const uint
             reg_sort<6>(d, mm, lane);
         } else if (mm <= 128) {
             reg_sort<7>(d, mm, lane);
-        } else if (mm <= 256) {
-            reg_sort<8>(d, mm, lane);
-        } else if (mm <= 512) {
-            reg_sort<9>(d, mm, lane);
         } else {
-            reg_sort<10>(d, mm, lane);
+            reg_sort<8>(d, mm, lane);
         }
     }
 }

@@ -149,8 +149,9 @@ def test_lattice_closed_forms(J):
 def test_member_segments_of_every_length(J):
     # fully linked clumps (side 0.2 < b / sqrt(3)) far apart, with sizes on
     # both sides of every boundary of the segmented sort: one warp in
-    # registers up to 1024, one block in shared memory up to 8192, chunks
-    # beyond; input order shuffled so each halo's members arrive unsorted
+    # registers up to 256 (32, 64, 128 per network size), one block in shared
+    # memory up to 8192, chunks beyond; input order shuffled so each halo's
+    # members arrive unsorted
     rng = np.random.default_rng(7)
     sizes = [1, 2, 3, 31, 32, 33, 64, 65, 128, 129, 255, 257, 511, 513, 1000, 1024, 1025, 2047, 2049,
              4096, 8192, 8193, 12000]
