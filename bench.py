@@ -181,6 +181,30 @@ def time_oracle(spec, reps=1):
     return times
 
 
+def rank_spec(spec, rank: int, world: int):
+    """The box rank `rank` processes: the workload itself at N = 1, else an
+    independent replica with seed + rank (the units shard across ranks and no
+    data is exchanged)."""
+    if world <= 1:
+        return spec
+    return synth.BoxSpec(spec.name, spec.N, spec.L, spec.b, spec.n_halos, spec.frac, spec.seed + rank,
+                         spec.velocities, spec.min_size)
+
+
+def slowest_rank_ms(ms: float, dist, device) -> float:
+    """Time of the slowest rank (all-reduce MAX), identical on every rank."""
+    if dist is None:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, N: int, ms_per_step: float) -> float:
+    """Whole-job throughput: the particles of all ranks' boxes per second."""
+    return world * N / (ms_per_step * 1e-3)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -295,9 +319,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    spec = synth.BOX_1024 if args.workload == "1024" else synth.BOX_256
-    if world > 1:
-        spec = synth.BoxSpec(spec.name, spec.N, spec.L, spec.b, spec.n_halos, spec.frac, spec.seed + rank)
+    spec = rank_spec(synth.BOX_1024 if args.workload == "1024" else synth.BOX_256, rank, world)
     pos, vel = synth.generate(spec, device="cuda")
     torch.cuda.synchronize()
     N = spec.N
@@ -336,13 +358,11 @@ def main():
     trace = J.trace_read()
     J.trace_enable(False)
     J.sync()
+    ms = slowest_rank_ms(ms, dist, "cuda")
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     ms_per_step = ms / args.steps
-    value = world * N / (ms_per_step * 1e-3)
+    value = job_value(world, N, ms_per_step)
 
     # roofline of the dominant kernel (largest total time in the timed region)
     peak, peak_kind = load_peaks()
