@@ -91,7 +91,7 @@ int jfof_trace_read(jfof_ctx *ctx, char *buf, size_t len, size_t *written);
    `small_max` particles is "small" (one thread per particle); one with more
    than `dense_over` (and at most 65535) is "dense" (linked through its
    sub-cells; 0 disables that path); the rest are "medium" (one warp per
-   cell).  Defaults 8 and 64.  Labels do not depend on them; only speed does.
+   cell).  Defaults 8 and 96.  Labels do not depend on them; only speed does.
    Takes effect at the next jfof_bin_cells. */
 int jfof_set_cell_classes(jfof_ctx *ctx, int32_t small_max, int32_t dense_over);
 

@@ -159,7 +159,7 @@ def set_loop_budget(iterations: int, device=None):
     _check(library().jfof_set_loop_budget(context(device), int(iterations)), "jfof_set_loop_budget")
 
 
-def set_cell_classes(small_max: int = 8, dense_over: int = 64, device=None):
+def set_cell_classes(small_max: int = 8, dense_over: int = 96, device=None):
     """Link-step cell classes: <= small_max particles "small", > dense_over
     "dense" (sub-cell path; 0 disables it), the rest "medium"."""
     _check(library().jfof_set_cell_classes(context(device), int(small_max), int(dense_over)),

@@ -258,7 +258,7 @@ int jfof_autotune(jfof_ctx *ctx, const float *pos, int64_t N, float L, float b, 
         int n = int(n0 * f);
         if (n >= 3 && n <= nmax && n != n0) ns.push_back(n);
     }
-    const int cls[][2] = {{8, 64}, {4, 64}, {8, 128}, {16, 64}, {8, 32}, {4, 96}};
+    const int cls[][2] = {{8, 96}, {8, 64}, {4, 96}, {8, 128}, {16, 96}, {8, 48}};
     cudaSetDevice(ctx->device);
     cudaEvent_t t0, t1;
     cudaEventCreate(&t0);

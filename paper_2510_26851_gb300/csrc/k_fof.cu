@@ -480,7 +480,7 @@ __device__ __forceinline__ void lunite(int *lp, int a, int b) {
 // ---------------------------------------------------------------------------
 // Medium cells, local part: one warp per cell.  The cell's particles are
 // staged in shared memory and all their pairs tested (lane = one particle,
-// the other broadcast).  Up to 64 particles: adjacency bitmasks and a
+// the other broadcast).  Up to 96 particles: adjacency bitmasks and a
 // breadth-first search over them; larger cells: a shared-memory union-find
 // over local indices.  Then parent[slot] = first slot of the slot's local
 // component.  A cell larger than the staging area (possible only when it
@@ -583,6 +583,74 @@ __global__ void __launch_bounds__(32 * kMedWarps) medium_local_kernel(const floa
             __syncwarp();
             continue;
         }
+        if (mA <= 96) {
+            // The same for up to 96 particles: particles lane, lane+32 and
+            // lane+64, with 96-bit masks in three words (word indices are
+            // compile-time constants, so the masks stay in registers).
+            constexpr int R = 3;
+            float4 q[R];
+            bool hv[R];
+            uint32_t r[R][R];
+#pragma unroll
+            for (int h = 0; h < R; ++h) {
+                hv[h] = lane + 32 * h < mA;
+                q[h] = hv[h] ? sp[lane + 32 * h] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int wd = 0; wd < R; ++wd) r[h][wd] = (hv[h] && wd == h) ? 1u << lane : 0u;
+            }
+#pragma unroll
+            for (int wi = 0; wi < R; ++wi) {
+                const int iend = min(mA, 32 * wi + 32);
+                for (int i = 32 * wi; i < iend; ++i) {
+                    const float4 pi = sp[i];
+                    const uint32_t bi = 1u << (i & 31);
+#pragma unroll
+                    for (int h = 0; h < R; ++h)
+                        if (hv[h] && linked(pi, q[h], g)) r[h][wi] |= bi;
+                }
+            }
+            uint32_t unv[R];
+#pragma unroll
+            for (int wd = 0; wd < R; ++wd) {
+                const int c = min(max(mA - 32 * wd, 0), 32);
+                unv[wd] = c == 32 ? 0xffffffffu : (1u << c) - 1u;
+            }
+            int root[R] = {0, 0, 0};
+            while (unv[0] | unv[1] | unv[2]) {
+                const int sw = unv[0] ? 0 : (unv[1] ? 1 : 2);
+                const uint32_t su = sw == 0 ? unv[0] : (sw == 1 ? unv[1] : unv[2]);
+                const int sb = __ffs(int(su)) - 1, seed = 32 * sw + sb;
+                uint32_t comp[R], fr[R];
+#pragma unroll
+                for (int wd = 0; wd < R; ++wd) comp[wd] = fr[wd] = wd == sw ? 1u << sb : 0u;
+                while (fr[0] | fr[1] | fr[2]) {
+                    uint32_t nb[R];
+#pragma unroll
+                    for (int wd = 0; wd < R; ++wd) {
+                        uint32_t v = 0u;
+#pragma unroll
+                        for (int h = 0; h < R; ++h)
+                            if ((fr[h] >> lane) & 1u) v |= r[h][wd];
+                        nb[wd] = __reduce_or_sync(0xffffffffu, v);
+                    }
+#pragma unroll
+                    for (int wd = 0; wd < R; ++wd) {
+                        fr[wd] = nb[wd] & ~comp[wd];
+                        comp[wd] |= nb[wd];
+                    }
+                }
+#pragma unroll
+                for (int h = 0; h < R; ++h) {
+                    if ((comp[h] >> lane) & 1u) root[h] = seed;
+                    unv[h] &= ~comp[h];
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < R; ++h)
+                if (hv[h]) parent[a0 + lane + 32 * h] = int(a0) + root[h];
+            __syncwarp();
+            continue;
+        }
         for (int cb = 0; cb * 32 < mA; ++cb) {
             int j = cb * 32 + lane;
             bool has = j < mA;
@@ -608,7 +676,7 @@ __global__ void __launch_bounds__(32 * kMedWarps) medium_local_kernel(const floa
 // each entry.  Cached component representatives: equal values mean one
 // component, so such a linked pair needs no union; after a union every cached
 // value naming either side becomes the merged representative (a stale value
-// only costs an exact union).  A cell of more than 64 particles (possible
+// only costs an exact union).  A cell of more than 96 particles (possible
 // only when it cannot take the dense path) walks its neighbours one at a
 // time instead.
 constexpr int kMedXWarps = 8;
@@ -664,14 +732,17 @@ __global__ void __launch_bounds__(32 * kMedXWarps) medium_kernel(const float4 *_
         }
         int rep0 = lane < mA ? uf_find(parent, int(a0 + lane)) : -1;
         int rep1 = lane + 32 < mA ? uf_find(parent, int(a0 + lane + 32)) : -1;
-        if (mA <= 64) {
+        if (mA <= 96) {
+            int rep2 = lane + 64 < mA ? uf_find(parent, int(a0 + lane + 64)) : -1;
             const float4 pa0 = lane < mA ? spos[a0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
             const float4 pa1 = lane + 32 < mA ? spos[a0 + lane + 32] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 pa2 = lane + 64 < mA ? spos[a0 + lane + 64] : make_float4(0.f, 0.f, 0.f, 0.f);
             // neighbours to visit: small cells all round, medium forward
             const uint32_t cand = __ballot_sync(0xffffffffu, lane < 26 && (ncls == 1 || (ncls == 2 && lane < 13)));
             const uint32_t m0 = lane < mA ? reach_mask(pa0, cx, cy, cz, cand, g) : 0u;
             const uint32_t m1 = lane + 32 < mA ? reach_mask(pa1, cx, cy, cz, cand, g) : 0u;
-            const uint32_t reach = __reduce_or_sync(0xffffffffu, m0 | m1);
+            const uint32_t m2 = lane + 64 < mA ? reach_mask(pa2, cx, cy, cz, cand, g) : 0u;
+            const uint32_t reach = __reduce_or_sync(0xffffffffu, m0 | m1 | m2);
             const bool take = (reach >> lane) & 1u;
             const int c = take ? int(nb1 - nb0) : 0;
             int incl = c;
@@ -720,11 +791,12 @@ __global__ void __launch_bounds__(32 * kMedXWarps) medium_kernel(const float4 *_
                         const float4 qe = lq[e];
                         const int qse = lslot[e], oe = __float_as_int(qe.w);
                         int rb = lrep[e];
-                        const int nh = mA > 32 ? 2 : 1;
+                        const int nh = mA > 64 ? 3 : (mA > 32 ? 2 : 1);
                         for (int h = 0; h < nh; ++h) {
-                            const uint32_t mh = h ? m1 : m0;
-                            const int ra = h ? rep1 : rep0;
-                            const bool join = ((mh >> oe) & 1u) && ra != rb && linked(h ? pa1 : pa0, qe, g);
+                            const uint32_t mh = h == 0 ? m0 : (h == 1 ? m1 : m2);
+                            const int ra = h == 0 ? rep0 : (h == 1 ? rep1 : rep2);
+                            const bool join = ((mh >> oe) & 1u) && ra != rb &&
+                                              linked(h == 0 ? pa0 : (h == 1 ? pa1 : pa2), qe, g);
                             const int merged = join ? uf_unite_rep(parent, int(a0) + lane + 32 * h, qse, st) : 0;
                             unsigned um = __ballot_sync(0xffffffffu, join);
                             const int s2 = rb;
@@ -735,6 +807,7 @@ __global__ void __launch_bounds__(32 * kMedXWarps) medium_kernel(const float4 *_
                                 const int nr = __shfl_sync(0xffffffffu, merged, L);
                                 if (rep0 == s1 || rep0 == s2) rep0 = nr;
                                 if (rep1 == s1 || rep1 == s2) rep1 = nr;
+                                if (rep2 == s1 || rep2 == s2) rep2 = nr;
                                 if (rb == s1 || rb == s2) rb = nr;
                             }
                         }

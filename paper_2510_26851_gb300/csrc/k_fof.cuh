@@ -11,7 +11,7 @@ namespace jfof {
 constexpr int kSubSide = 9;
 constexpr int kSubMax = kSubSide * kSubSide * kSubSide;  // 729
 constexpr uint32_t kDenseMaxM = 65535;
-constexpr int kDefaultDenseThreshold = 64;
+constexpr int kDefaultDenseThreshold = 96;
 constexpr int kDefaultSmallThreshold = 8;
 constexpr int kCounters = 8;
 // Output-order buckets of the label scatter (at most this many).
