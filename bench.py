@@ -385,6 +385,11 @@ def main():
                 "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": algo_bytes, "launch_ms": per_launch_ms}
     kernels = {k: {"launches": c, "ms_per_step": t / args.steps} for k, (c, t) in trace.items()}
+    # a1-a7 alone (labels and groups, without the halo properties): the same
+    # timed steps less the property launches' event time
+    props_ms = trace.get("halo_props", (0, 0.0))[1] / args.steps
+    fof_ms = ms_per_step - props_ms
+    a1_a7 = {"ms_per_step": fof_ms, "value": job_value(world, N, fof_ms), "unit": UNIT}
 
     # end to end through the C ABI's host-buffer call (jfof_fof_host): pinned
     # host inputs uploaded (the velocity upload overlapping the FoF kernels),
@@ -460,7 +465,7 @@ def main():
                        "l2": "inputs (24 GiB) larger than L2; no flush",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-            "gpu_launches": launches * args.steps, "kernels": kernels,
+            "gpu_launches": launches * args.steps, "kernels": kernels, "a1_a7": a1_a7,
         }
         line.update(extras)
         print(json.dumps(line), flush=True)
