@@ -667,20 +667,56 @@ __global__ void __launch_bounds__(32 * kMedWarps) medium_local_kernel(const floa
     }
 }
 
+// ---------------------------------------------------------------------------
+// Warp task runner: every lane brings c tasks (emit(put) hands them to put in
+// a fixed order); the warp lays them out in a shared-memory window of cap
+// entries at a time and all lanes then take them in turn (work(task)).
+template <class Emit, class Work>
+__device__ __forceinline__ void warp_tasks(int c, uint32_t *buf, int cap, int lane, Emit emit, Work work) {
+    int pre = c;
+    for (int o = 1; o < 32; o <<= 1) {
+        int v = __shfl_up_sync(0xffffffffu, pre, o);
+        if (lane >= o) pre += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, pre, 31);
+    pre -= c;
+    for (int w0 = 0; w0 < total; w0 += cap) {
+        if (c > 0 && pre < w0 + cap && pre + c > w0) {
+            int idx = pre;
+            emit([&](uint32_t task) {
+                if (idx >= w0 && idx < w0 + cap) buf[idx - w0] = task;
+                ++idx;
+            });
+        }
+        __syncwarp();
+        const int nt = min(cap, total - w0);
+        for (int t = lane; t < nt; t += 32) work(buf[t]);
+        __syncwarp();
+    }
+}
+
+// Box of sub-cells, inclusive per axis.
+struct SubBox {
+    int x0, y0, z0, x1, y1, z1;
+};
+
 // Medium cells, cross part: one warp per cell A.  Every particle of a small
 // neighbour (any direction) or a medium forward neighbour that lies within
 // reach of A is gathered, with the offset of its cell, into a shared-memory
 // list (the neighbours' particles are spread over the lanes as one flat
-// range); the list is then swept by the whole warp, each lane pairing its
-// particles of A that reach that offset (a 26-bit mask per particle) with
-// each entry.  Cached component representatives: equal values mean one
-// component, so such a linked pair needs no union; after a union every cached
-// value naming either side becomes the merged representative (a stale value
-// only costs an exact union).  A cell of more than 96 particles (possible
-// only when it cannot take the dense path) walks its neighbours one at a
-// time instead.
+// range); the list is then swept as flat (entry, particle of A) tasks over
+// the particles of A that reach the entry's offset (a 26-bit reach mask per
+// particle, and per offset the set of particles that reach it).  Cached
+// component representatives (one per particle of A, one per entry): a value
+// is always a node that was in the entity's component at some time, so equal
+// values mean one component and such a linked pair needs no union; a union
+// stores the merged representative on both sides (a stale value only costs
+// an exact union).  A cell of more than 96 particles (possible only when it
+// cannot take the dense path) walks its neighbours one at a time instead.
 constexpr int kMedXWarps = 8;
 constexpr int kMedList = 64;
+constexpr int kMedA = 96;        // cells up to this size take the list path
+constexpr int kMedTaskCap = 256;
 
 // Offsets o in cand whose neighbour cell p can reach (gap <= 1.02 b).
 __device__ __forceinline__ uint32_t reach_mask(float4 p, int cx, int cy, int cz, uint32_t cand, const LinkGeom &g) {
@@ -706,9 +742,17 @@ __global__ void __launch_bounds__(32 * kMedXWarps) medium_kernel(const float4 *_
     __shared__ int sh_slot[kMedXWarps][kMedList];
     __shared__ int sh_rep[kMedXWarps][kMedList];
     __shared__ int sh_pre[kMedXWarps][32];
+    __shared__ float4 sh_pa[kMedXWarps][kMedA];
+    __shared__ int sh_repa[kMedXWarps][kMedA];
+    __shared__ uint32_t sh_amask[kMedXWarps][26][3];
+    __shared__ uint32_t sh_task[kMedXWarps][kMedTaskCap];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     float4 *lq = sh_q[w];
     int *lslot = sh_slot[w], *lrep = sh_rep[w], *pre = sh_pre[w];
+    float4 *spa = sh_pa[w];
+    int *repa = sh_repa[w];
+    uint32_t(*amask)[3] = sh_amask[w];
+    uint32_t *tasks = sh_task[w];
     // this lane's neighbour offset (lanes < 26), packed for shuffles
     const int my_off = lane < 26 ? (c_nb26[lane][0] + 1) | (c_nb26[lane][1] + 1) << 2 | (c_nb26[lane][2] + 1) << 4
                                  : 0;
@@ -732,7 +776,7 @@ __global__ void __launch_bounds__(32 * kMedXWarps) medium_kernel(const float4 *_
         }
         int rep0 = lane < mA ? uf_find(parent, int(a0 + lane)) : -1;
         int rep1 = lane + 32 < mA ? uf_find(parent, int(a0 + lane + 32)) : -1;
-        if (mA <= 96) {
+        if (mA <= kMedA) {
             int rep2 = lane + 64 < mA ? uf_find(parent, int(a0 + lane + 64)) : -1;
             const float4 pa0 = lane < mA ? spos[a0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
             const float4 pa1 = lane + 32 < mA ? spos[a0 + lane + 32] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -743,6 +787,31 @@ __global__ void __launch_bounds__(32 * kMedXWarps) medium_kernel(const float4 *_
             const uint32_t m1 = lane + 32 < mA ? reach_mask(pa1, cx, cy, cz, cand, g) : 0u;
             const uint32_t m2 = lane + 64 < mA ? reach_mask(pa2, cx, cy, cz, cand, g) : 0u;
             const uint32_t reach = __reduce_or_sync(0xffffffffu, m0 | m1 | m2);
+            // the cell's particles, their representatives, and per offset the set
+            // of particles that reach it (three 32-bit words)
+            if (lane < mA) {
+                spa[lane] = pa0;
+                repa[lane] = rep0;
+            }
+            if (lane + 32 < mA) {
+                spa[lane + 32] = pa1;
+                repa[lane + 32] = rep1;
+            }
+            if (lane + 64 < mA) {
+                spa[lane + 64] = pa2;
+                repa[lane + 64] = rep2;
+            }
+            for (uint32_t rb = reach; rb; rb &= rb - 1u) {
+                const int o = __ffs(int(rb)) - 1;
+                const uint32_t w0 = __ballot_sync(0xffffffffu, (m0 >> o) & 1u);
+                const uint32_t w1 = __ballot_sync(0xffffffffu, (m1 >> o) & 1u);
+                const uint32_t w2 = __ballot_sync(0xffffffffu, (m2 >> o) & 1u);
+                if (lane == 0) {
+                    amask[o][0] = w0;
+                    amask[o][1] = w1;
+                    amask[o][2] = w2;
+                }
+            }
             const bool take = (reach >> lane) & 1u;
             const int c = take ? int(nb1 - nb0) : 0;
             int incl = c;
@@ -784,33 +853,31 @@ __global__ void __launch_bounds__(32 * kMedXWarps) medium_kernel(const float4 *_
                 nl += __popc(bal);
                 __syncwarp();
                 if (nl > kMedList - 32 || (t0 + 32 >= total && nl > 0)) {
-                    // sweep the list: every lane pairs its particles of A with each entry
+                    // sweep the list as flat (entry, particle of A) tasks: only the
+                    // particles of A that reach the entry's offset
                     for (int e = lane; e < nl; e += 32) lrep[e] = uf_find(parent, lslot[e]);
                     __syncwarp();
-                    for (int e = 0; e < nl; ++e) {
-                        const float4 qe = lq[e];
-                        const int qse = lslot[e], oe = __float_as_int(qe.w);
-                        int rb = lrep[e];
-                        const int nh = mA > 64 ? 3 : (mA > 32 ? 2 : 1);
-                        for (int h = 0; h < nh; ++h) {
-                            const uint32_t mh = h == 0 ? m0 : (h == 1 ? m1 : m2);
-                            const int ra = h == 0 ? rep0 : (h == 1 ? rep1 : rep2);
-                            const bool join = ((mh >> oe) & 1u) && ra != rb &&
-                                              linked(h == 0 ? pa0 : (h == 1 ? pa1 : pa2), qe, g);
-                            const int merged = join ? uf_unite_rep(parent, int(a0) + lane + 32 * h, qse, st) : 0;
-                            unsigned um = __ballot_sync(0xffffffffu, join);
-                            const int s2 = rb;
-                            while (um) {
-                                const int L = __ffs(um) - 1;
-                                um &= um - 1u;
-                                const int s1 = __shfl_sync(0xffffffffu, ra, L);
-                                const int nr = __shfl_sync(0xffffffffu, merged, L);
-                                if (rep0 == s1 || rep0 == s2) rep0 = nr;
-                                if (rep1 == s1 || rep1 == s2) rep1 = nr;
-                                if (rep2 == s1 || rep2 == s2) rep2 = nr;
-                                if (rb == s1 || rb == s2) rb = nr;
-                            }
-                        }
+                    for (int eb = 0; eb < nl; eb += 32) {
+                        const int e = eb + lane;
+                        const int oe = e < nl ? __float_as_int(lq[e].w) : 0;
+                        const int ce = e < nl ? __popc(amask[oe][0]) + __popc(amask[oe][1]) + __popc(amask[oe][2]) : 0;
+                        warp_tasks(
+                            ce, tasks, kMedTaskCap, lane,
+                            [&](auto put) {
+#pragma unroll
+                                for (int wd = 0; wd < 3; ++wd)
+                                    for (uint32_t bits = amask[oe][wd]; bits; bits &= bits - 1u)
+                                        put(uint32_t(e) | uint32_t(32 * wd + __ffs(int(bits)) - 1) << 8);
+                            },
+                            [&](uint32_t t) {
+                                const int te = int(t & 255u), ta = int(t >> 8);
+                                if (repa[ta] == lrep[te]) return;
+                                if (linked(spa[ta], lq[te], g)) {
+                                    const int m = uf_unite_rep(parent, int(a0) + ta, lslot[te], st);
+                                    repa[ta] = m;
+                                    lrep[te] = m;
+                                }
+                            });
                     }
                     __syncwarp();
                     nl = 0;
@@ -1124,39 +1191,6 @@ __global__ void __launch_bounds__(32 * kDenseWarps) dense_cells_kernel(float4 *_
         __syncwarp();
     }
 }
-
-// ---------------------------------------------------------------------------
-// Warp task runner: every lane brings c tasks (emit(put) hands them to put in
-// a fixed order); the warp lays them out in a shared-memory window of cap
-// entries at a time and all lanes then take them in turn (work(task)).
-template <class Emit, class Work>
-__device__ __forceinline__ void warp_tasks(int c, uint32_t *buf, int cap, int lane, Emit emit, Work work) {
-    int pre = c;
-    for (int o = 1; o < 32; o <<= 1) {
-        int v = __shfl_up_sync(0xffffffffu, pre, o);
-        if (lane >= o) pre += v;
-    }
-    const int total = __shfl_sync(0xffffffffu, pre, 31);
-    pre -= c;
-    for (int w0 = 0; w0 < total; w0 += cap) {
-        if (c > 0 && pre < w0 + cap && pre + c > w0) {
-            int idx = pre;
-            emit([&](uint32_t task) {
-                if (idx >= w0 && idx < w0 + cap) buf[idx - w0] = task;
-                ++idx;
-            });
-        }
-        __syncwarp();
-        const int nt = min(cap, total - w0);
-        for (int t = lane; t < nt; t += 32) work(buf[t]);
-        __syncwarp();
-    }
-}
-
-// Box of sub-cells, inclusive per axis.
-struct SubBox {
-    int x0, y0, z0, x1, y1, z1;
-};
 
 // Non-empty sub-cells of a dense cell (occupancy rows) inside box b: f(G)
 // for each, in a fixed order.
