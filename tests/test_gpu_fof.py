@@ -323,3 +323,102 @@ def test_host_buffer_step_matches_device_path(J):
     J.sync()
     assert dv3 is None and torch.equal(r3.label, r.label)
     assert torch.equal(p3.com[:H], p.com[:H]) and torch.equal(p3.mass[:H], p.mass[:H])
+
+
+def _min_image(d, L):
+    return d - L * torch.round(d / L)
+
+
+def _select(pos, ref, lo, hi, L, chunk=1 << 27):
+    # indices of particles whose min-image offset from ref lies in [lo, hi]
+    # per axis (float32, in chunks; the margins used are many ulp wide)
+    out = []
+    for s0 in range(0, pos.shape[0], chunk):
+        rel = _min_image(pos[s0:s0 + chunk] - ref, L)
+        out.append(torch.nonzero(((rel >= lo) & (rel <= hi)).all(1)).squeeze(1) + s0)
+    return torch.cat(out)
+
+
+def test_box_1024cubed_sampled(J):
+    # The bench's workload and launch configuration (2^30 particles, default
+    # grid and cell classes, jfof_fof then jfof_halo_props).  Checked by
+    # properties that hold at any size and, on samples, against the oracle.
+    spec = synth.BOX_1024
+    pos, vel = synth.generate(spec, device="cuda")
+    r = J.fof(pos, spec.L, spec.b, spec.min_size)
+    p = J.halo_props(pos, vel, spec.L, r.groups)
+    J.sync()
+    N, L, b = spec.N, spec.L, spec.b
+    g = r.groups
+    H = g.n_halos
+    # labels: label[i] is the smallest index of i's group, so label <= index
+    # and labels are fixed points
+    lab = r.label.long()
+    assert bool((lab <= torch.arange(N, device="cuda")).all())
+    assert bool((lab[lab] == lab).all())
+    # groups from the labels (plain torch): count per raw label, the cut,
+    # halo ids ascending by raw label, CSR starts
+    cnt = torch.bincount(lab, minlength=N)
+    kept = cnt >= spec.min_size
+    assert H == int(kept.sum())
+    rank = torch.cumsum(kept, 0) - 1
+    want_hid = torch.where(kept[lab], rank[lab], torch.full_like(lab, -1))
+    assert torch.equal(g.halo_id.long(), want_hid)
+    del want_hid, rank
+    want_cnt = cnt[kept]
+    assert torch.equal(g.count[:H].long(), want_cnt)
+    hs = g.halo_start[:H + 1].long()
+    assert int(hs[0]) == 0 and torch.equal(hs[1:] - hs[:-1], want_cnt)
+    M = int(hs[H])
+    assert M == int((g.halo_id >= 0).sum())
+    # members: each segment holds its halo's particles, ascending
+    mem = g.members[:M].long()
+    seg = torch.repeat_interleave(torch.arange(H, device="cuda"), want_cnt)
+    assert torch.equal(g.halo_id.long()[mem], seg)
+    same = seg[1:] == seg[:-1]
+    assert bool((mem[1:][same] > mem[:-1][same]).all())
+    del cnt, kept, seg, same, lab
+    torch.cuda.empty_cache()
+
+    rng = np.random.default_rng(7)
+    counts = g.count[:H]
+    picks = list(rng.choice(H, 12, replace=False)) + [int(torch.argmax(counts))]
+    for h in picks:
+        s0, s1 = int(hs[h]), int(hs[h + 1])
+        m = mem[s0:s1]
+        pm = pos[m].double()
+        # neighbourhood: everything within 2 b of the halo's box (min image
+        # about its first member)
+        ref = pm[0]
+        rel = _min_image(pm - ref, L)
+        lo, hi = rel.min(0).values - 2 * b, rel.max(0).values + 2 * b
+        sel = _select(pos, ref.float(), lo.float(), hi.float(), L)
+        is_mem = torch.isin(sel, m)
+        assert int(is_mem.sum()) == s1 - s0
+        lab_s = oracle.fof_brute(pos[sel].cpu().numpy(), L, b)
+        mlab = lab_s[is_mem.cpu().numpy()]
+        # the members form one group, and nothing outside it links to them
+        assert (mlab == mlab[0]).all(), h
+        assert not (lab_s[~is_mem.cpu().numpy()] == mlab[0]).any(), h
+        # FP64 properties of this halo (members in ascending index order)
+        hid0 = np.zeros(s1 - s0, np.int32)
+        m_ref, com_ref, vm_ref, sg_ref = oracle.halo_props(pm.cpu().numpy(), vel[m].double().cpu().numpy(),
+                                                            hid0, 1, L)
+        assert float(p.mass[h]) == float(m_ref[0])
+        dcom = np.abs(p.com[h].double().cpu().numpy() - com_ref[0])
+        dcom = np.minimum(dcom, L - dcom)
+        assert (dcom <= COM_TOL * L).all(), (h, dcom)
+        scale = float(vel[m].double().norm(dim=1).mean())
+        assert (np.abs(p.vmean[h].double().cpu().numpy() - vm_ref[0]) <= VMEAN_TOL * scale + 1e-6).all(), h
+        assert abs(float(p.sigv[h]) - sg_ref[0]) <= SIGV_RTOL * sg_ref[0] + 1e-6, h
+    # random sub-cubes: particles linked inside a cube share a label
+    for _ in range(8):
+        c = torch.tensor(rng.uniform(0.0, L, 3), device="cuda", dtype=torch.float32)
+        sel = _select(pos, c, torch.full((3,), -2.0, device="cuda"), torch.full((3,), 2.0, device="cuda"), L)
+        lab_s = oracle.fof_brute(pos[sel].cpu().numpy(), L, b)
+        glab = r.label[sel].cpu().numpy()
+        for comp in np.unique(lab_s):
+            members_c = glab[lab_s == comp]
+            assert (members_c == members_c[0]).all()
+    del pos, vel, r, p
+    torch.cuda.empty_cache()
