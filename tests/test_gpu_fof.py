@@ -169,6 +169,29 @@ def test_member_segments_of_every_length(J):
     assert H == len(sizes)
 
 
+def test_split_entry_points_bin_link_groups(J):
+    # jfof_bin_cells -> jfof_link (labels only, through the bucketed scatter)
+    # -> jfof_groups (groups of given labels): the oracle's labels and groups;
+    # 300k particles take 74 scatter buckets of 4096, 4.5M the 1024-bucket
+    # limit with wider buckets
+    import types
+    for N, L, nh, seed in ((300_000, 67.0, 1500, 21), (4_500_000, 160.0, 25_000, 22)):
+        spec = synth.BoxSpec("t", N, L, synth.linking_length(L, N), nh, 0.6, seed, velocities=False)
+        pos, _ = synth.generate(spec, device="cuda", velocities=False)
+        pos_np = pos.cpu().numpy()
+        lab_ref = oracle.fof_labels(pos_np, spec.L, spec.b)
+        grid = J.bin_cells(pos, spec.L, spec.b)
+        lab = J.link(grid)
+        J.sync()
+        assert np.array_equal(lab.cpu().numpy(), lab_ref)
+        g = J.groups(lab, spec.min_size)
+        J.sync()
+        check_groups(types.SimpleNamespace(groups=g), g.n_halos, lab_ref, spec.min_size)
+        g2 = J.groups(torch.from_numpy(lab_ref).cuda(), spec.min_size)
+        J.sync()
+        check_groups(types.SimpleNamespace(groups=g2), g2.n_halos, lab_ref, spec.min_size)
+
+
 def test_wrap_flag_and_boundary(J):
     rng = np.random.default_rng(4)
     N, L, b = 30000, 12.0, 0.25
