@@ -445,3 +445,29 @@ def test_box_1024cubed_sampled(J):
             assert (members_c == members_c[0]).all()
     del pos, vel, r, p
     torch.cuda.empty_cache()
+
+
+def test_side_stream_and_tracing(J):
+    # calls enqueue on torch's current stream; with tracing on, every launch
+    # is recorded under its kernel name
+    spec = synth.BoxSpec("t", 150_000, 55.0, synth.linking_length(55.0, 150_000), 800, 0.6, 31, velocities=False)
+    pos, _ = synth.generate(spec, device="cuda", velocities=False)
+    ref = J.fof(pos, spec.L, spec.b, spec.min_size)
+    J.sync()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    J.trace_enable(True)
+    try:
+        with torch.cuda.stream(side):
+            r = J.fof(pos, spec.L, spec.b, spec.min_size)
+            J.sync()
+            tr = J.trace_read()
+    finally:
+        J.trace_enable(False)
+    torch.cuda.current_stream().wait_stream(side)
+    assert torch.equal(r.label, ref.label)
+    assert torch.equal(r.groups.halo_id, ref.groups.halo_id)
+    for name in ("bin_count", "bin_scatter", "brick_sort", "link_small", "link_medium", "finalize_roots",
+                 "finalize_labels", "segsort"):
+        assert name in tr and tr[name][0] >= 1, (name, sorted(tr))
+    assert all(t >= 0.0 for _, t in tr.values())
