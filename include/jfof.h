@@ -342,7 +342,7 @@ int jfof_fof_host(jfof_ctx *ctx, const float *h_pos, const float *h_vel, int64_t
    fixed 16 MiB device array inside the library, present on every GPU that
    loads it until the process exits; the call allocates nothing.
    Limit: jfof_fof_all_bytes(N, n_axis) must not exceed 16 MiB (about
-   1.3e5 particles at the default grid); larger inputs return JFOF_ENOMEM
+   1.9e5 particles at the default grid); larger inputs return JFOF_ENOMEM
    before any work is enqueued.
    The first call on a device looks up the array's device address with that
    device current (a synchronous runtime call); make that first call before
