@@ -113,7 +113,10 @@ class ClockSampler:
     def __init__(self, device_index: int):
         self.dev = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+        # raw samples (the JSON line carries their summary); JFOF_CLOCKS_DIR keeps them
+        import tempfile
+        out_dir = os.environ.get("JFOF_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"jfof_clocks_rank{device_index}.csv")
 
     def start(self):
         try:
