@@ -2,6 +2,9 @@
 candidate list, the device exponential and edge uniforms, per-sample labels
 and halo counts (bit-exact), and the score-function gradient against the
 FP64 oracle with identical draws."""
+import os
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 import pytest
 import torch
@@ -71,14 +74,37 @@ def test_pairs_bit_exact(J, form):
     assert np.array_equal(pr.p.cpu().numpy().view(np.uint32), pp.view(np.uint32))
 
 
+def oracle_pairs(pos, L, b, form=0, coef=None):
+    """The oracle's candidate list, computed from the positions alone."""
+    coef = oracle.prob_coef(b, form) if coef is None else coef
+    return oracle.pairs(pos.cpu().numpy(), L, b, r_cut_of(b), form, coef)
+
+
+def assert_same_pairs(pr, ref):
+    pi, pj, pd, pp = ref
+    assert pr.E == len(pi)
+    assert np.array_equal(pr.i.cpu().numpy(), pi) and np.array_equal(pr.j.cpu().numpy(), pj)
+    assert np.array_equal(pr.d.cpu().numpy().view(np.uint32), pd.view(np.uint32))
+    assert np.array_equal(pr.p.cpu().numpy().view(np.uint32), pp.view(np.uint32))
+
+
+def seeded_advantage(K, seed):
+    """Advantages A_k with sum 0, drawn on the host (independent of the GPU)."""
+    a = np.random.default_rng(seed).standard_normal(K)
+    a -= a.mean()
+    return a
+
+
 def test_samples_and_halo_counts_bit_exact(J):
     spec, pos = small_box()
     pr = J.pairs(pos, spec.L, spec.b)
+    J.sync()
+    pi, pj, pd, pp = oracle_pairs(pos, spec.L, spec.b)
+    assert_same_pairs(pr, (pi, pj, pd, pp))
     K, seed = 13, 42  # K not a multiple of 4 or of the sample chunk
     labels, nh = J.reinforce_sample(pr, K, seed, spec.min_size)
     J.sync()
-    ref_l, ref_n = oracle.reinforce_sample(spec.N, pr.i.cpu().numpy(), pr.j.cpu().numpy(),
-                                           pr.p.cpu().numpy(), K, seed, spec.min_size)
+    ref_l, ref_n = oracle.reinforce_sample(spec.N, pi, pj, pp, K, seed, spec.min_size)
     assert np.array_equal(labels.cpu().numpy(), ref_l)
     assert np.array_equal(nh.cpu().numpy(), ref_n)
     # samples differ from one another and from plain FoF
@@ -90,14 +116,15 @@ def test_gradient_matches_fp64_oracle(J, form):
     spec, pos = small_box(N=30_000, L=48.0, seed=4)
     coef = J.prob_coef(spec.b, form, alpha=0.5)
     pr = J.pairs(pos, spec.L, spec.b, prob_form=form, coef=coef)
-    K, seed = 64, 7
-    _, nh = J.reinforce_sample(pr, K, seed, 5)
-    Ls = nh.float()
-    adv = (Ls - Ls.mean()).contiguous()
-    g = J.reinforce_grad(pos, pr, K, seed, adv)
     J.sync()
-    ref = oracle.reinforce_grad(pos.cpu().numpy(), spec.L, pr.i.cpu().numpy(), pr.j.cpu().numpy(),
-                                pr.p.cpu().numpy(), K, seed, adv.cpu().numpy().astype(np.float64), form, coef)
+    pi, pj, pd, pp = oracle_pairs(pos, spec.L, spec.b, form, coef)
+    assert_same_pairs(pr, (pi, pj, pd, pp))
+    K, seed = 64, 7
+    adv = seeded_advantage(K, 100 + form)
+    g = J.reinforce_grad(pos, pr, K, seed, torch.from_numpy(adv.astype(np.float32)).cuda())
+    J.sync()
+    ref = oracle.reinforce_grad(pos.cpu().numpy(), spec.L, pi, pj, pp, K, seed,
+                                adv.astype(np.float32).astype(np.float64), form, coef)
     got = g.cpu().numpy().astype(np.float64)
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     assert np.linalg.norm(ref) > 0 and err <= GRAD_RTOL, err
@@ -123,12 +150,10 @@ def test_dense_clump_pairs_and_gradient(J):
     assert np.array_equal(pr.i.cpu().numpy(), pi) and np.array_equal(pr.j.cpu().numpy(), pj)
     assert np.array_equal(pr.p.cpu().numpy().view(np.uint32), pp.view(np.uint32))
     K, seed = 8, 3
-    _, nh = J.reinforce_sample(pr, K, seed, 5)
-    Ls = nh.float()
-    adv = (Ls - Ls.mean() + torch.arange(K, device="cuda", dtype=torch.float32) * 0.1).contiguous()
-    g = J.reinforce_grad(pos, pr, K, seed, adv)
+    adv = seeded_advantage(K, 9).astype(np.float32)
+    g = J.reinforce_grad(pos, pr, K, seed, torch.from_numpy(adv).cuda())
     J.sync()
-    ref = oracle.reinforce_grad(pos_np, L, pi, pj, pp, K, seed, adv.cpu().numpy().astype(np.float64), 0, coef)
+    ref = oracle.reinforce_grad(pos_np, L, pi, pj, pp, K, seed, adv.astype(np.float64), 0, coef)
     got = g.cpu().numpy().astype(np.float64)
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     assert np.linalg.norm(ref) > 0 and err <= GRAD_RTOL, err
@@ -150,30 +175,32 @@ def test_autograd_function(J):
 
 
 def test_diff_box_128cubed_full_size(J):
-    # the 128^3 differentiable-mode box: full pair list bit-exact; three of the
-    # 256 samples bit-exact; the gradient on a sampled particle subset
+    # the 128^3 differentiable-mode box (K = 256): the full pair list
+    # bit-exact against the oracle's own list; 16 of the 256 samples (labels
+    # and halo counts) bit-exact, the oracle fed only its own list; the
+    # gradient on a sampled particle subset with host-drawn advantages
     spec = synth.DIFF_128
     pos, _ = synth.generate(spec, device="cuda", velocities=False)
     pos_np = pos.cpu().numpy()
     pr = J.pairs(pos, spec.L, spec.b)
     J.sync()
-    pi, pj, pd, pp = oracle.pairs(pos_np, spec.L, spec.b, r_cut_of(spec.b), 0, J.prob_coef(spec.b, 0))
-    assert np.array_equal(pr.i.cpu().numpy(), pi) and np.array_equal(pr.j.cpu().numpy(), pj)
-    assert np.array_equal(pr.p.cpu().numpy().view(np.uint32), pp.view(np.uint32))
+    pi, pj, pd, pp = oracle_pairs(pos, spec.L, spec.b)
+    assert_same_pairs(pr, (pi, pj, pd, pp))
     K, seed = 256, 0
     labels, nh = J.reinforce_sample(pr, K, seed, spec.min_size)
     J.sync()
-    for k in (0, 5, 255):
-        lab, h = oracle.reinforce_sample_one(spec.N, pi, pj, pp, k, seed, spec.min_size)
+    ks = [0, 1, 2, 3, 5, 17, 64, 100, 127, 128, 129, 200, 211, 233, 254, 255]
+    with ThreadPoolExecutor(max_workers=min(len(ks), os.cpu_count() or 1)) as ex:
+        refs = list(ex.map(lambda k: oracle.reinforce_sample_one(spec.N, pi, pj, pp, k, seed, spec.min_size), ks))
+    for k, (lab, h) in zip(ks, refs):
         assert np.array_equal(labels[k].cpu().numpy(), lab), k
         assert nh[k].item() == h
-    Ls = nh.float()
-    adv = (Ls - Ls.mean()).contiguous()
-    g = J.reinforce_grad(pos, pr, K, seed, adv).cpu().numpy().astype(np.float64)
+    adv = seeded_advantage(K, 128).astype(np.float32)
+    g = J.reinforce_grad(pos, pr, K, seed, torch.from_numpy(adv).cuda()).cpu().numpy().astype(np.float64)
     mask = np.zeros(spec.N, np.uint8)
     mask[np.random.default_rng(2).choice(spec.N, 3000, replace=False)] = 1
-    ref = oracle.reinforce_grad_masked(pos_np, spec.L, pi, pj, pp, K, seed,
-                                       adv.cpu().numpy().astype(np.float64), 0, J.prob_coef(spec.b, 0), mask)
+    ref = oracle.reinforce_grad_masked(pos_np, spec.L, pi, pj, pp, K, seed, adv.astype(np.float64), 0,
+                                       J.prob_coef(spec.b, 0), mask)
     sel = mask.astype(bool)
     err = np.linalg.norm(g[sel] - ref[sel]) / np.linalg.norm(ref[sel])
     assert err <= GRAD_RTOL, err

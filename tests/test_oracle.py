@@ -83,6 +83,42 @@ def test_cell_list_equals_brute_force_near_boundary():
     assert spans
 
 
+# The threaded oracle (slabs of cell layers, Sec. 2.3's union-find fusion with
+# threads for devices) must give the sequential oracle's labels, which the
+# brute-force pins above fix, for any thread count and grid -- including more
+# threads than layers (empty slabs) and one-layer slabs whose every pair
+# crosses into a neighbour slab.
+
+@pytest.mark.parametrize("threads", [1, 2, 3, 5, 8])
+def test_threaded_labels_equal_sequential_uniform(threads):
+    N, L = 3000, 10.0
+    pos = synth.uniform(N, L, 0).numpy()
+    b = 0.55 * L / N ** (1 / 3)
+    bf = oracle.fof_brute(pos, L, b)
+    for n in (0, 1, 3, 4, 7, oracle.max_cells_per_axis(L, b)):
+        assert np.array_equal(oracle.fof_labels_mt(pos, L, b, n_axis=n, threads=threads), bf), (n, threads)
+
+
+def test_threaded_labels_equal_sequential_clustered_and_boundary():
+    spec = synth.BoxSpec("t", 20000, 40.0, synth.linking_length(40.0, 20000) * 1.5, 120, 0.6, 4)
+    pos, _ = synth.generate(spec, velocities=False)
+    pos = pos.numpy()
+    seq = oracle.fof_labels(pos, spec.L, spec.b)
+    assert len(set(seq.tolist())) < 20000 - 1000
+    for t in (2, 4, 7, 16):
+        assert np.array_equal(oracle.fof_labels_mt(pos, spec.L, spec.b, threads=t), seq), t
+    # particles hugging the periodic faces: slab 0 and the last slab link
+    rng = np.random.default_rng(6)
+    L, b = 10.0, 0.4
+    q = rng.uniform(0, L, (4000, 3))
+    q[:, 2] = np.where(rng.random(4000) < 0.5, rng.uniform(0, 0.3, 4000), rng.uniform(L - 0.3, L, 4000))
+    q = q.astype(np.float32)
+    bf = oracle.fof_brute(q, L, b)
+    assert any(bf[i] != i for i in range(4000))
+    for t in (2, 3, 6):
+        assert np.array_equal(oracle.fof_labels_mt(q, L, b, threads=t), bf), t
+
+
 @pytest.mark.parametrize("m", [4, 7])
 def test_cubic_lattice_closed_form(m):
     # lattice spacing a: a = 0.9 b -> one periodic group; a = 1.1 b -> singletons
@@ -246,6 +282,41 @@ def test_props_closed_forms():
     vel2 = np.tile(np.array([[3.0, 4.0, 5.0]], np.float32), (8, 1))
     _, _, _, sg = oracle.halo_props(pos, vel2, hid, 1, L)
     assert sg[0] == 0.0
+
+
+def _cold_halo_with_outlier(n=2400, L=100.0, seed=21):
+    """A cold, fast halo whose smallest-index member is a velocity outlier and
+    sits at the halo's edge (positions and velocities in binary32)."""
+    rng = np.random.default_rng(seed)
+    c = np.array([L - 0.05, 0.02, 50.0])  # straddles two periodic faces
+    pos = (c + rng.normal(0.0, 0.03, (n, 3))) % L
+    pos[0] = (c + np.array([0.25, -0.2, 0.22])) % L
+    v0 = np.array([812.0, -640.0, 377.0])
+    vel = v0 + rng.normal(0.0, 0.05, (n, 3))
+    vel[0] = v0 + np.array([900.0, -750.0, 820.0])  # outlier, ~2e4 sigma away
+    return pos.astype(np.float32), vel.astype(np.float32), L
+
+
+def test_props_cold_halo_with_outlier_first_member():
+    # velocity dispersion (population, 1-D) of a cold halo whose reference
+    # member is an outlier: FP64 two-pass oracle == numpy's variance of the
+    # 3n deviations (a library routine), and the periodic COM == the plain
+    # mean of the unwrapped positions
+    pos, vel, L = _cold_halo_with_outlier()
+    n = pos.shape[0]
+    hid = np.zeros(n, np.int32)
+    m, com, vm, sg = oracle.halo_props(pos.astype(np.float64), vel.astype(np.float64), hid, 1, L)
+    v64 = vel.astype(np.float64)
+    assert np.allclose(vm[0], v64.mean(0), rtol=0, atol=1e-12)
+    want = math.sqrt(np.var(v64 - v64.mean(0), axis=0, ddof=0).sum() / 3.0)
+    assert abs(sg[0] - want) <= 1e-12 * want
+    unwrapped = pos.astype(np.float64).copy()
+    ref0 = unwrapped[0].copy()
+    unwrapped = ref0 + (unwrapped - ref0 + L / 2) % L - L / 2
+    assert np.allclose(com[0], unwrapped.mean(0) % L, rtol=0, atol=1e-9)
+    # the outlier dominates the one-pass sums shifted by it: |vbar - v_r|^2 /
+    # sigma^2 is about 3n, so such a sum would lose about 3n ulp of sigma^2
+    assert np.sum((vm[0] - v64[0]) ** 2) / sg[0] ** 2 > 2 * n
 
 
 def test_props_unassigned_ignored_and_two_halos():
@@ -498,3 +569,57 @@ def test_reinforce_sample_matches_plain_fof_when_p_is_step():
         assert np.array_equal(labels[k], ref)
     _, cnt = oracle.groups(ref, 20)
     assert (nh == len(cnt)).all()
+
+
+# --------------------------------------------------------------------------
+# Restricted helpers used by the full-size checks (Sec. 3.2, Eqs. 6-8): each
+# must equal the unrestricted function it restricts, which the pins above fix.
+
+def _reinforce_box():
+    spec = synth.BoxSpec("t", 3000, 24.0, synth.linking_length(24.0, 3000) * 1.3, 30, 0.6, 11)
+    pos, _ = synth.generate(spec, velocities=False)
+    pos = pos.numpy()
+    b = spec.b
+    rc = float(np.float32(1.5 * np.float32(b)))
+    coef = oracle.prob_coef(b, 0)
+    pi, pj, pd, pp = oracle.pairs(pos, spec.L, b, rc, 0, coef)
+    assert len(pi) > 2000
+    return spec, pos, pi, pj, pp, coef
+
+
+def test_reinforce_sample_one_is_a_row_of_the_full_sample():
+    spec, pos, pi, pj, pp, _ = _reinforce_box()
+    K, seed = 9, 0x5EED  # K not a multiple of the four samples one Philox call serves
+    labels, nh = oracle.reinforce_sample(spec.N, pi, pj, pp, K, seed, 5)
+    rows = set()
+    for k in range(K):
+        lab, h = oracle.reinforce_sample_one(spec.N, pi, pj, pp, k, seed, 5)
+        assert np.array_equal(lab, labels[k]), k
+        assert h == nh[k], k
+        rows.add(lab.tobytes())
+    assert len(rows) == K  # every sample differs: a wrong sample index fails
+    # a different seed draws different samples
+    lab0, _ = oracle.reinforce_sample_one(spec.N, pi, pj, pp, 0, seed + 1, 5)
+    assert not np.array_equal(lab0, labels[0])
+
+
+def test_reinforce_grad_masked_restricts_the_full_gradient():
+    spec, pos, pi, pj, pp, coef = _reinforce_box()
+    K, seed = 12, 77
+    A = np.random.default_rng(4).standard_normal(K)
+    A -= A.mean()
+    for form, c in ((0, coef), (1, oracle.prob_coef(spec.b, 1, alpha=0.5))):
+        full = oracle.reinforce_grad(pos, spec.L, pi, pj, pp, K, seed, A, form, c)
+        assert np.abs(full).max() > 0
+        ones = np.ones(spec.N, np.uint8)
+        g1 = oracle.reinforce_grad_masked(pos, spec.L, pi, pj, pp, K, seed, A, form, c, ones)
+        assert np.array_equal(g1, full)
+        # a mask that splits many pairs: rows inside equal the full rows
+        # (their partners outside still contribute), rows outside stay 0
+        mask = (np.random.default_rng(5).random(spec.N) < 0.5).astype(np.uint8)
+        inside = mask.astype(bool)
+        split = np.count_nonzero(inside[pi] != inside[pj])
+        assert split > 100
+        gm = oracle.reinforce_grad_masked(pos, spec.L, pi, pj, pp, K, seed, A, form, c, mask)
+        assert np.array_equal(gm[inside], full[inside])
+        assert not gm[~inside].any()
