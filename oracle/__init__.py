@@ -39,7 +39,7 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11",
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-pthread",
            "-D_DEFAULT_SOURCE", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
@@ -62,6 +62,9 @@ def _load():
         lib.orc_fof_labels.restype = c.c_int
         lib.orc_fof_labels.argtypes = [_f32p, c.c_int64, c.c_float, c.c_float,
                                        c.c_int32, _i32p]
+        lib.orc_fof_labels_mt.restype = c.c_int
+        lib.orc_fof_labels_mt.argtypes = [_f32p, c.c_int64, c.c_float, c.c_float,
+                                          c.c_int32, c.c_int32, _i32p]
         lib.orc_fof_brute.restype = c.c_int
         lib.orc_fof_brute.argtypes = [_f32p, c.c_int64, c.c_float, c.c_float, _i32p]
         lib.orc_groups.restype = c.c_int64
@@ -130,6 +133,26 @@ def fof_labels(pos, L: float, b: float, n_axis: int = 0) -> np.ndarray:
     st = _load().orc_fof_labels(p, p.shape[0], np.float32(L), np.float32(b), n_axis, lab)
     if st != 0:
         raise OracleError(f"orc_fof_labels status {st}")
+    return lab
+
+
+def default_threads() -> int:
+    """Threads for the threaded oracle: the cores this process may run on."""
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:
+        return max(1, os.cpu_count() or 1)
+
+
+def fof_labels_mt(pos, L: float, b: float, n_axis: int = 0, threads: int = 0) -> np.ndarray:
+    """The labels of :func:`fof_labels` computed on several threads (slabs of
+    cell layers, pairs across slabs united afterwards)."""
+    p = _pos32(pos)
+    lab = np.empty(p.shape[0], np.int32)
+    t = threads if threads > 0 else default_threads()
+    st = _load().orc_fof_labels_mt(p, p.shape[0], np.float32(L), np.float32(b), n_axis, t, lab)
+    if st != 0:
+        raise OracleError(f"orc_fof_labels_mt status {st}")
     return lab
 
 

@@ -53,6 +53,7 @@
  * central finite differences, Philox known-answer vectors, exact enumeration
  * of tiny REINFORCE graphs.
  */
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -303,6 +304,275 @@ int orc_fof_labels(const float *pos, int64_t N, float L, float b, int32_t n_axis
         label[i] = uf_find(parent, (int32_t)i);
     cell_list_free(&cl);
     return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The same labels on T threads, for boxes too large for one core.           */
+/*                                                                            */
+/* The cells are cut into T slabs of whole z-layers; cells are numbered       */
+/* z-major, so the particles of a slab are one contiguous run of cell-list    */
+/* slots.  Thread t visits the pairs (i, j), i < j, whose particle i lies in  */
+/* its slab -- the pairs orc_fof_labels tests from i's side, so every pair is */
+/* tested exactly once -- with the same predicate.  A linked pair with both   */
+/* slots in the slab is united at once in a forest over slots (the smaller    */
+/* slot is the root, so thread t reads and writes only its own slots); a      */
+/* linked pair with one slot in another slab is recorded.  The recorded pairs */
+/* are then united one after another in thread order.  Both sides unite       */
+/* exactly the linked pairs, so the components equal those of the sequential  */
+/* union-find, and label[i] = smallest original index in i's component        */
+/* (Sec. 2 step (v)) is the same.  This is the slab decomposition with        */
+/* union-find fusion of Sec. 2.3, with threads in place of devices.           */
+
+
+typedef struct {
+    const float *pos;
+    const cell_list *cl;
+    int64_t lo, hi;      /* work range of a parallel phase */
+    float inv_cell;
+    int64_t *cid;
+    int32_t *parent;
+    int32_t *root;
+    int32_t *minidx;
+    int32_t *label;
+    int64_t *fill;
+    /* linking */
+    float L, b2;
+    int64_t s0, s1;      /* slots of the slab */
+    int64_t *cross;      /* recorded pairs of slots (a, k) */
+    int64_t ncross, capcross;
+    int status;
+} mt_job;
+
+static void mt_run(mt_job *jobs, int T, void *(*fn)(void *))
+{
+    pthread_t th[256];
+    int started[256];
+    for (int t = 0; t < T; ++t)
+        started[t] = pthread_create(&th[t], NULL, fn, &jobs[t]) == 0;
+    for (int t = 0; t < T; ++t) {
+        if (started[t])
+            pthread_join(th[t], NULL);
+        else
+            fn(&jobs[t]); /* no thread: run the share here */
+    }
+}
+
+static void *mt_cell_ids(void *arg)
+{
+    mt_job *jb = (mt_job *)arg;
+    int32_t n = jb->cl->n;
+    for (int64_t i = jb->lo; i < jb->hi; ++i) {
+        int32_t ix = cell_coord(jb->pos[3 * i + 0], jb->inv_cell, n);
+        int32_t iy = cell_coord(jb->pos[3 * i + 1], jb->inv_cell, n);
+        int32_t iz = cell_coord(jb->pos[3 * i + 2], jb->inv_cell, n);
+        jb->cid[i] = ix + (int64_t)n * (iy + (int64_t)n * iz);
+        __atomic_fetch_add(&jb->cl->start[jb->cid[i] + 1], 1, __ATOMIC_RELAXED);
+    }
+    return NULL;
+}
+
+static void *mt_fill(void *arg)
+{
+    mt_job *jb = (mt_job *)arg;
+    const cell_list *cl = jb->cl;
+    for (int64_t i = jb->lo; i < jb->hi; ++i) {
+        int64_t k = __atomic_fetch_add(&jb->fill[jb->cid[i]], 1, __ATOMIC_RELAXED);
+        cl->idx[k] = (int32_t)i;
+        cl->cpos[3 * k + 0] = jb->pos[3 * i + 0];
+        cl->cpos[3 * k + 1] = jb->pos[3 * i + 1];
+        cl->cpos[3 * k + 2] = jb->pos[3 * i + 2];
+    }
+    return NULL;
+}
+
+static int mt_record(mt_job *jb, int64_t a, int64_t k)
+{
+    if (jb->ncross == jb->capcross) {
+        int64_t cap = jb->capcross ? 2 * jb->capcross : 4096;
+        int64_t *p = (int64_t *)realloc(jb->cross, sizeof(int64_t) * 2 * (size_t)cap);
+        if (!p)
+            return ORC_ENOMEM;
+        jb->cross = p;
+        jb->capcross = cap;
+    }
+    jb->cross[2 * jb->ncross] = a;
+    jb->cross[2 * jb->ncross + 1] = k;
+    jb->ncross += 1;
+    return ORC_OK;
+}
+
+static void *mt_link_slab(void *arg)
+{
+    mt_job *jb = (mt_job *)arg;
+    const cell_list *cl = jb->cl;
+    for (int64_t c = jb->lo; c < jb->hi && jb->status == ORC_OK; ++c) {
+        if (cl->start[c] == cl->start[c + 1])
+            continue;
+        int64_t nb[27];
+        int nnb = neighbour_cells(cl, c, nb);
+        for (int64_t a = cl->start[c]; a < cl->start[c + 1]; ++a) {
+            int32_t i = cl->idx[a];
+            for (int s = 0; s < nnb; ++s)
+                for (int64_t k = cl->start[nb[s]]; k < cl->start[nb[s] + 1]; ++k) {
+                    if (cl->idx[k] <= i)
+                        continue; /* each unordered pair once, from its smaller index */
+                    if (!(orc_dist2(cl->cpos + 3 * a, cl->cpos + 3 * k, jb->L) <= jb->b2))
+                        continue;
+                    if (k >= jb->s0 && k < jb->s1)
+                        uf_union(jb->parent, (int32_t)a, (int32_t)k);
+                    else if (mt_record(jb, a, k) != ORC_OK)
+                        jb->status = ORC_ENOMEM;
+                }
+        }
+    }
+    return NULL;
+}
+
+/* root of each slot, with no writes (the forest is complete) */
+static void *mt_roots(void *arg)
+{
+    mt_job *jb = (mt_job *)arg;
+    for (int64_t a = jb->lo; a < jb->hi; ++a) {
+        int32_t r = (int32_t)a;
+        while (jb->parent[r] != r)
+            r = jb->parent[r];
+        jb->root[a] = r;
+    }
+    return NULL;
+}
+
+/* smallest original index per root */
+static void *mt_minidx(void *arg)
+{
+    mt_job *jb = (mt_job *)arg;
+    for (int64_t a = jb->lo; a < jb->hi; ++a) {
+        int32_t *m = &jb->minidx[jb->root[a]], v = jb->cl->idx[a];
+        int32_t cur = __atomic_load_n(m, __ATOMIC_RELAXED);
+        while (v < cur && !__atomic_compare_exchange_n(m, &cur, v, 0, __ATOMIC_RELAXED, __ATOMIC_RELAXED))
+            ;
+    }
+    return NULL;
+}
+
+static void *mt_labels(void *arg)
+{
+    mt_job *jb = (mt_job *)arg;
+    for (int64_t a = jb->lo; a < jb->hi; ++a)
+        jb->label[jb->cl->idx[a]] = jb->minidx[jb->root[a]];
+    return NULL;
+}
+
+static void mt_split(mt_job *jobs, int T, int64_t total)
+{
+    for (int t = 0; t < T; ++t) {
+        jobs[t].lo = total * t / T;
+        jobs[t].hi = total * (t + 1) / T;
+    }
+}
+
+int orc_fof_labels_mt(const float *pos, int64_t N, float L, float b, int32_t n_axis,
+                      int32_t nthreads, int32_t *label)
+{
+    if (N < 1 || !(L > 0.0f) || !(b > 0.0f) || !(b < 0.5f * L) || nthreads < 1)
+        return ORC_EINVAL;
+    for (int64_t i = 0; i < 3 * N; ++i)
+        if (!(pos[i] >= 0.0f && pos[i] < L))
+            return ORC_ERANGE;
+    int32_t nmax = orc_max_cells_per_axis(L, b);
+    int32_t n = n_axis > 0 ? n_axis : oracle_grid(N, L, b);
+    if (n > nmax || n == 2)
+        return ORC_EINVAL;
+    int T = nthreads > 256 ? 256 : nthreads;
+    cell_list cl;
+    cl.n = n;
+    cl.ncell = (int64_t)n * n * n;
+    cl.start = (int64_t *)calloc((size_t)cl.ncell + 1, sizeof(int64_t));
+    cl.idx = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    cl.cpos = (float *)malloc(sizeof(float) * 3 * (size_t)N);
+    int64_t *cid = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+    mt_job *jobs = (mt_job *)calloc((size_t)T, sizeof(mt_job));
+    int32_t *parent = NULL, *root = NULL, *minidx = NULL;
+    int64_t *fill = NULL;
+    int st = ORC_ENOMEM;
+    if (!cl.start || !cl.idx || !cl.cpos || !cid || !jobs)
+        goto done;
+    for (int t = 0; t < T; ++t) {
+        jobs[t].pos = pos;
+        jobs[t].cl = &cl;
+        jobs[t].inv_cell = (float)((double)n / (double)L);
+        jobs[t].cid = cid;
+        jobs[t].L = L;
+        jobs[t].b2 = b * b;
+    }
+    /* cell list: counts, offsets, then slots (order inside a cell is free) */
+    mt_split(jobs, T, N);
+    mt_run(jobs, T, mt_cell_ids);
+    for (int64_t c = 0; c < cl.ncell; ++c)
+        cl.start[c + 1] += cl.start[c];
+    fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)cl.ncell);
+    if (!fill)
+        goto done;
+    memcpy(fill, cl.start, sizeof(int64_t) * (size_t)cl.ncell);
+    for (int t = 0; t < T; ++t)
+        jobs[t].fill = fill;
+    mt_run(jobs, T, mt_fill);
+    free(fill);
+    fill = NULL;
+    free(cid);
+    cid = NULL;
+    /* slabs of z-layers, linked in parallel */
+    parent = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    if (!parent)
+        goto done;
+    for (int64_t a = 0; a < N; ++a)
+        parent[a] = (int32_t)a;
+    int64_t layer = (int64_t)n * n;
+    for (int t = 0; t < T; ++t) {
+        int64_t z0 = (int64_t)n * t / T, z1 = (int64_t)n * (t + 1) / T;
+        jobs[t].lo = z0 * layer;
+        jobs[t].hi = z1 * layer;
+        jobs[t].s0 = cl.start[z0 * layer];
+        jobs[t].s1 = cl.start[z1 * layer];
+        jobs[t].parent = parent;
+        jobs[t].status = ORC_OK;
+    }
+    mt_run(jobs, T, mt_link_slab);
+    for (int t = 0; t < T; ++t)
+        if (jobs[t].status != ORC_OK)
+            goto done;
+    /* pairs across slabs, one after another */
+    for (int t = 0; t < T; ++t)
+        for (int64_t e = 0; e < jobs[t].ncross; ++e)
+            uf_union(parent, (int32_t)jobs[t].cross[2 * e], (int32_t)jobs[t].cross[2 * e + 1]);
+    /* label = smallest original index of the component */
+    root = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    minidx = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    if (!root || !minidx)
+        goto done;
+    for (int64_t a = 0; a < N; ++a)
+        minidx[a] = INT32_MAX;
+    mt_split(jobs, T, N);
+    for (int t = 0; t < T; ++t) {
+        jobs[t].root = root;
+        jobs[t].minidx = minidx;
+        jobs[t].label = label;
+    }
+    mt_run(jobs, T, mt_roots);
+    mt_run(jobs, T, mt_minidx);
+    mt_run(jobs, T, mt_labels);
+    st = ORC_OK;
+done:
+    if (jobs)
+        for (int t = 0; t < T; ++t)
+            free(jobs[t].cross);
+    free(jobs);
+    free(fill);
+    free(cid);
+    free(parent);
+    free(root);
+    free(minidx);
+    cell_list_free(&cl);
+    return st;
 }
 
 /* O(N^2) brute force over all pairs with the same predicate (pin for the
