@@ -646,8 +646,9 @@ def autotune(pos: torch.Tensor, L: float, b: float, min_size: int = 20, reps: in
 def fof_static(pos: torch.Tensor, L: float, b: float, min_size: int = 20, n_axis: int = 0,
                wrap: bool = False, out: FofResult | None = None) -> FofResult:
     """a1-a7 like :func:`fof`, with the library's fixed 16 MiB device scratch
-    instead of a workspace (for callers that must not allocate device memory;
-    about 1.3e5 particles at most).  Calls sharing a GPU must not overlap."""
+    instead of a workspace (for callers that must not allocate device memory).
+    Limit: ``fof_all_bytes(N, n) <= 16 MiB``, about 1.9e5 particles at the
+    default grid.  Calls sharing a GPU must not overlap."""
     _need(pos, torch.float32, None, "pos")
     N = pos.shape[0]
     dev = pos.device

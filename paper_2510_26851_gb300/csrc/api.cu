@@ -1,5 +1,6 @@
 // api.cu -- the C ABI (include/jfof.h): argument checks, workspace layout,
 // launches on the context's stream, and the latched device status.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 
@@ -102,6 +103,21 @@ size_t fof_layout(int64_t N, int n, FofBuffers *fb, void *base) {
     return off;
 }
 
+// SM count of the current device, queried once per device (GB300: 152).
+int num_sms() {
+    constexpr int kMaxDevices = 64;
+    static std::atomic<int> cache[kMaxDevices];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+    if (dev >= kMaxDevices) dev = kMaxDevices - 1;
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+    cache[dev].store(sms, std::memory_order_relaxed);
+    return sms;
+}
+
 }  // namespace jfof
 
 extern "C" {
@@ -123,6 +139,10 @@ int jfof_create(jfof_ctx **ctx, int device, void *stream) {
     if (!ctx) return JFOF_EINVAL;
     *ctx = nullptr;
     if (cudaSetDevice(device) != cudaSuccess) return JFOF_ECUDA;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms < 1)
+        return JFOF_ECUDA;
+    (void)num_sms();  // launch grids are sized by this device's SM count from here on
     jfof_ctx *c = new jfof_ctx();
     c->device = device;
     c->tracer = nullptr;

@@ -42,16 +42,17 @@ int jfof_fof_host(jfof_ctx *ctx, const float *h_pos, const float *h_vel, int64_t
     const size_t bytes = sizeof(float) * 3 * size_t(N);
     if (cudaMemcpyAsync(d_pos, h_pos, bytes, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) return JFOF_ECUDA;
     if (h_vel) {
-        cudaEventRecord(ctx->ev_pos, ctx->stream);
-        cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_pos, 0);
-        if (cudaMemcpyAsync(d_vel, h_vel, bytes, cudaMemcpyHostToDevice, ctx->copy_stream) != cudaSuccess)
+        if (cudaEventRecord(ctx->ev_pos, ctx->stream) != cudaSuccess ||
+            cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_pos, 0) != cudaSuccess ||
+            cudaMemcpyAsync(d_vel, h_vel, bytes, cudaMemcpyHostToDevice, ctx->copy_stream) != cudaSuccess ||
+            cudaEventRecord(ctx->ev_vel, ctx->copy_stream) != cudaSuccess)
             return JFOF_ECUDA;
-        cudaEventRecord(ctx->ev_vel, ctx->copy_stream);
     }
     e = jfof_fof(ctx, d_pos, N, L, b, n, flags, min_size, ws, ws_bytes, label, halo_id, count, halo_start, members,
                  n_halos);
-    // the context's stream never runs ahead of the velocity upload
-    if (h_vel) cudaStreamWaitEvent(ctx->stream, ctx->ev_vel, 0);
+    // the context's stream never runs ahead of the velocity upload (waited on
+    // even when jfof_fof failed, so the copy stream is never left behind)
+    if (h_vel && cudaStreamWaitEvent(ctx->stream, ctx->ev_vel, 0) != cudaSuccess && !e) e = JFOF_ECUDA;
     if (e) return e;
     int64_t H_cap = N / min_size;
     if (H_cap < 1) H_cap = 1;

@@ -10,16 +10,17 @@
 namespace jfof {
 
 // ---------------------------------------------------------------------------
-// Launch geometry: GB300 has 152 SMs; grid-stride kernels launch a multiple of
-// that so every SM gets the same number of resident CTAs.
-constexpr int kNumSMs = 152;
+// Launch geometry: grid-stride kernels launch a multiple of the current
+// device's SM count (152 on GB300), queried once per device, so every SM gets
+// the same number of resident CTAs.
+int num_sms();
 constexpr int kBrick = 16;                  // cells per brick side
 constexpr int kBrickCells = kBrick * kBrick * kBrick;
 constexpr int64_t kDefaultLoopBudget = int64_t(1) << 24;
 
 inline int grid_for(int64_t work, int threads, int per_sm = 8) {
     int64_t want = (work + threads - 1) / threads;
-    int64_t cap = int64_t(kNumSMs) * per_sm;
+    int64_t cap = int64_t(num_sms()) * per_sm;
     if (want < 1) want = 1;
     return int(want < cap ? want : cap);
 }

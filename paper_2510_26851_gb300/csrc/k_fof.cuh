@@ -17,9 +17,10 @@ constexpr int kCounters = 8;
 // Output-order buckets of the label scatter (at most this many).
 constexpr int kTailBuckets = 1024;
 // Binning of grids with at most kFewBricks bricks: a counting sort by
-// kFewGrid CTAs over contiguous chunks (no global atomics).
+// kFewGrid CTAs over contiguous chunks (no global atomics).  The chunk count
+// is fixed (two per SM of a GB300); results do not depend on it.
 constexpr int kFewBricks = 4096;
-constexpr int kFewGrid = 2 * kNumSMs;
+constexpr int kFewGrid = 304;
 
 // One IEEE binary32 multiply on the host (b*b for the link threshold).
 inline float host_mul(float a, float b) {

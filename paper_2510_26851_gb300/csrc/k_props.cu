@@ -49,14 +49,19 @@ __device__ __forceinline__ float load_coord(const float *pos, int64_t i, int a, 
     return wrap ? wrap_coord(x, L) : x;
 }
 
-// One warp per halo (grid-stride over halos), one gather pass over the
-// members.  Positions are summed as minimum-image offsets from the halo's
-// first member xr (periodic centre of mass); velocities as offsets from that
-// member's velocity vr, with the squares of those offsets summed alongside,
-// so the dispersion needs no second pass:
-//   vmean = vr + S1/m,  sigma^2 = (S2/m - |S1/m|^2) / 3,
-// S1 = sum(v - vr), S2 = sum |v - vr|^2 (compensated).  vr is a member, so
-// |S1/m| is of the order of sigma and the subtraction loses O(1) bits.
+// One warp per halo (grid-stride over halos).  Pass 1 gathers the members:
+// positions are summed as minimum-image offsets from the halo's first member
+// xr (periodic centre of mass) and velocities as offsets from that member's
+// velocity vr, giving vmean = vr + S1/m.  Pass 2 sums |v - vmean|^2 about
+// that mean (the dispersion of the design notes, two-pass): no cancellation
+// between large terms, whatever vr is (a cold halo whose first member is a
+// velocity outlier included).  The first 64 members' velocities stay in
+// registers between the passes; larger halos gather them again (L2 hits).
+__device__ __forceinline__ void load_vel(const float *__restrict__ vel, int64_t i, float v[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) v[a] = vel[3 * i + a];
+}
+
 __global__ void __launch_bounds__(256) halo_props_kernel(const float *__restrict__ pos, const float *__restrict__ vel,
                                                          float L, bool wrap, const int32_t *__restrict__ halo_start,
                                                          const int32_t *__restrict__ members,
@@ -81,7 +86,7 @@ __global__ void __launch_bounds__(256) halo_props_kernel(const float *__restrict
         }
         KSum sx[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         KSum sv[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-        KSum s2 = {0.f, 0.f};
+        float c0[3] = {0.f, 0.f, 0.f}, c1[3] = {0.f, 0.f, 0.f};  // members hs+lane, hs+lane+32
         for (int k0 = hs + lane; k0 < he; k0 += 64) {
             // two members per lane per step: all six gathers issue before the sums
             int k1 = k0 + 32;
@@ -93,9 +98,16 @@ __global__ void __launch_bounds__(256) halo_props_kernel(const float *__restrict
             for (int a = 0; a < 3; ++a) {
                 p0[a] = load_coord(pos, i0, a, L, wrap);
                 p1[a] = load_coord(pos, i1, a, L, wrap);
-                if (vel) {
-                    v0[a] = vel[3 * int64_t(i0) + a];
-                    v1[a] = vel[3 * int64_t(i1) + a];
+            }
+            if (vel) {
+                load_vel(vel, i0, v0);
+                load_vel(vel, i1, v1);
+            }
+            if (k0 == hs + lane) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    c0[a] = v0[a];
+                    c1[a] = v1[a];
                 }
             }
 #pragma unroll
@@ -106,32 +118,44 @@ __global__ void __launch_bounds__(256) halo_props_kernel(const float *__restrict
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     kadd(sx[a], min_image(p[a], xr[a], L, hL));
-                    if (vel) {
-                        float d = __fsub_rn(v[a], vr[a]);
-                        kadd(sv[a], d);
-                        kadd(s2, __fmul_rn(d, d));
-                    }
+                    if (vel) kadd(sv[a], __fsub_rn(v[a], vr[a]));
                 }
             }
         }
-        float dm[3];
-        float dd = 0.f;
+        float vm[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             float d = __fdiv_rn(kval(kwarp(sx[a])), fm);
             float c = wrap_coord(__fadd_rn(xr[a], d), L);
             if (lane == 0) com[3 * h + a] = c;
-            dm[a] = vel ? __fdiv_rn(kval(kwarp(sv[a])), fm) : 0.f;
-            dd = __fadd_rn(dd, __fmul_rn(dm[a], dm[a]));
+            vm[a] = vel ? __fadd_rn(vr[a], __fdiv_rn(kval(kwarp(sv[a])), fm)) : 0.f;
         }
         if (lane == 0) mass[h] = __fmul_rn(particle_mass, fm);
         if (!vel) continue;
-        float q = __fdiv_rn(kval(kwarp(s2)), fm);
-        float var = fmaxf(__fdiv_rn(__fsub_rn(q, dd), 3.0f), 0.f);
+        // pass 2: squared deviations from the mean
+        KSum s2 = {0.f, 0.f};
+        auto dev2 = [&](const float v[3]) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                float d = __fsub_rn(v[a], vm[a]);
+                kadd(s2, __fmul_rn(d, d));
+            }
+        };
+        if (m <= 64) {
+            if (lane < m) dev2(c0);
+            if (lane + 32 < m) dev2(c1);
+        } else {
+            for (int k = hs + lane; k < he; k += 32) {
+                float v[3];
+                load_vel(vel, members[k], v);
+                dev2(v);
+            }
+        }
+        float var = __fdiv_rn(kval(kwarp(s2)), __fmul_rn(3.0f, fm));
         if (lane == 0) {
 #pragma unroll
-            for (int a = 0; a < 3; ++a) vmean[3 * h + a] = __fadd_rn(vr[a], dm[a]);
-            sigv[h] = __fsqrt_rn(var);
+            for (int a = 0; a < 3; ++a) vmean[3 * h + a] = vm[a];
+            sigv[h] = __fsqrt_rn(fmaxf(var, 0.f));
         }
     }
 }

@@ -2,6 +2,8 @@
 one CUDA-graph launch give, box by box, the oracle's labels, halo ids and
 halo counts; the per-box loop gives the same; graph replays are stable; the
 autotuner's choice leaves labels unchanged."""
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 import pytest
 import torch
@@ -73,13 +75,15 @@ def test_batch_of_64_uneven_boxes(J):
     lab_l, hid_l, nh_l = [t.cpu().numpy().copy() for t in bt.run(pos, use_graph=False)]
     J.sync()
     assert np.array_equal(lab_g, lab_l) and np.array_equal(hid_g, hid_l) and np.array_equal(nh_g, nh_l)
-    # oracle on the four smallest boxes and one mid-size box
-    sizes = np.diff(off)
-    pick = list(np.argsort(sizes)[:4]) + [int(np.argsort(sizes)[len(sizes) // 2])]
+    # every box against the oracle (boxes on parallel host threads)
     pos_np = pos.cpu().numpy()
-    for k in pick:
+
+    def one(k):
         s, e = off[k], off[k + 1]
         check_box(J, pos_np[s:e], specs[k], lab_g[s:e], hid_g[s:e], nh_g[k])
+
+    with ThreadPoolExecutor(max_workers=oracle.default_threads()) as ex:
+        list(ex.map(one, range(len(specs))))
 
 
 def test_autotuner_choice_keeps_labels(J):

@@ -284,6 +284,27 @@ def test_props_and_backward_clustered_box(J):
         assert (err <= BWD_RTOL * np.abs(want) + 1e-6 * np.abs(want).max()).all(), err.max()
 
 
+def test_props_cold_halo_with_outlier_first_member(J):
+    # a 2400-member cold halo (bulk ~ 1100) whose smallest-index member is a
+    # velocity outlier at the halo's edge, plus a uniform background: sigma_v
+    # within 1e-4 of the FP64 oracle (a one-pass sum shifted by that member
+    # loses about 3n = 7200 ulp of sigma^2 here), COM within 1e-5 L
+    from test_oracle import _cold_halo_with_outlier
+    hp, hv, L = _cold_halo_with_outlier()
+    rng = np.random.default_rng(3)
+    nb = 40_000
+    bp = rng.uniform(0, L, (nb, 3)).astype(np.float32)
+    bv = rng.normal(0, 300, (nb, 3)).astype(np.float32)
+    pos_np = np.concatenate([hp, bp])
+    vel_np = np.concatenate([hv, bv])
+    b = float(np.float32(0.2 * L / (len(pos_np) ** (1 / 3))))
+    lab_ref = oracle.fof_labels(pos_np, L, b)
+    pos, r, H = run_fof(J, pos_np, L, b, 20)
+    assert np.array_equal(r.label.cpu().numpy(), lab_ref)
+    assert np.all(lab_ref[:len(hp)] == 0)  # the halo is one group, led by the outlier
+    props_check(J, pos, torch.from_numpy(vel_np).cuda(), r, H, L, lab_ref, 20)
+
+
 def test_autograd_function(J):
     spec = synth.BoxSpec("t", 50_000, 40.0, synth.linking_length(40.0, 50_000), 300, 0.6, 6)
     pos, vel = synth.generate(spec, device="cuda")
@@ -305,6 +326,34 @@ def test_autograd_function(J):
     exp_gv[mem] = (2 * w[:, None] / (3 * cnt[:, None]))[hid[mem]] * (vel.detach()[mem] - vm.detach()[hid[mem]])
     assert torch.allclose(pos.grad, exp_gp, rtol=1e-4, atol=1e-6 * exp_gp.abs().max().item())
     assert torch.allclose(vel.grad, exp_gv, rtol=1e-4, atol=1e-6 * exp_gv.abs().max().item())
+
+
+def test_diff_box_128cubed_frozen_adjoint(J):
+    # the 128^3 differentiable-mode box itself: labels and groups against the
+    # oracle, properties within tolerance, and the adjoint of
+    # L = sum_h w_h (|com_h|^2 + sigma_h^2), w_h ~ U(0,1), against the FP64
+    # analytic adjoint of the oracle
+    spec = synth.DIFF_128
+    pos, vel = synth.generate(spec, device="cuda")
+    pos_np = pos.cpu().numpy()
+    lab_ref = oracle.fof_labels(pos_np, spec.L, spec.b)
+    _, r, H = run_fof(J, pos_np, spec.L, spec.b, spec.min_size)
+    assert np.array_equal(r.label.cpu().numpy(), lab_ref)
+    check_groups(r, H, lab_ref, spec.min_size)
+    p, hid_ref, cnt_ref, ref = props_check(J, pos, vel, r, H, spec.L, lab_ref, spec.min_size)
+    w = np.random.default_rng(1).uniform(0.0, 1.0, H)
+    g_com = torch.zeros(r.groups.H_cap, 3, device="cuda")
+    g_sig = torch.zeros(r.groups.H_cap, device="cuda")
+    g_com[:H] = torch.from_numpy(2 * w[:, None] * p.com[:H].cpu().numpy()).float().cuda()
+    g_sig[:H] = torch.from_numpy(2 * w * p.sigv[:H].cpu().numpy()).float().cuda()
+    gp, gv = J.halo_props_backward(vel, r.groups, p.vmean, p.sigv, g_com=g_com, g_sigv=g_sig)
+    J.sync()
+    gp_ref, gv_ref = oracle.halo_props_backward(
+        vel.cpu().numpy().astype(np.float64), hid_ref, H, p.vmean[:H].cpu().numpy(),
+        p.sigv[:H].cpu().numpy(), g_com=g_com[:H].cpu().numpy(), g_sigv=g_sig[:H].cpu().numpy())
+    for got, want in ((gp.cpu().numpy(), gp_ref), (gv.cpu().numpy(), gv_ref)):
+        err = np.abs(got - want)
+        assert (err <= BWD_RTOL * np.abs(want) + 1e-6 * np.abs(want).max()).all(), err.max()
 
 
 def test_box_256cubed_full_parity(J):
@@ -362,10 +411,12 @@ def _select(pos, ref, lo, hi, L, chunk=1 << 27):
     return torch.cat(out)
 
 
-def test_box_1024cubed_sampled(J):
+def test_box_1024cubed(J):
     # The bench's workload and launch configuration (2^30 particles, default
     # grid and cell classes, jfof_fof then jfof_halo_props).  Checked by
-    # properties that hold at any size and, on samples, against the oracle.
+    # properties that hold at any size, every label and halo id against the
+    # threaded oracle (all cores of the host: 16 Grace cores on a GB300 machine),
+    # and on sampled halos the FP64 properties.
     spec = synth.BOX_1024
     pos, vel = synth.generate(spec, device="cuda")
     r = J.fof(pos, spec.L, spec.b, spec.min_size)
@@ -402,6 +453,17 @@ def test_box_1024cubed_sampled(J):
     assert bool((mem[1:][same] > mem[:-1][same]).all())
     del cnt, kept, seg, same, lab
     torch.cuda.empty_cache()
+    # every label and halo id against the threaded oracle (cell grid n = 1024;
+    # labels do not depend on it), counts against its groups
+    threads = oracle.default_threads()
+    lab_ref = oracle.fof_labels_mt(pos.cpu().numpy(), L, b, n_axis=1024, threads=threads)
+    assert np.array_equal(r.label.cpu().numpy(), lab_ref)
+    hid_ref, cnt_ref = oracle.groups(lab_ref, spec.min_size)
+    del lab_ref
+    assert H == len(cnt_ref)
+    assert np.array_equal(g.halo_id.cpu().numpy(), hid_ref)
+    assert np.array_equal(g.count[:H].cpu().numpy(), cnt_ref)
+    del hid_ref, cnt_ref
 
     rng = np.random.default_rng(7)
     counts = g.count[:H]
