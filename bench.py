@@ -17,7 +17,7 @@ path (weak scaling).  Rank 0 prints one JSON line.
 
 --impl reference times the plain CPU oracle on a bounded sample of the same
 workload (a 128^3 box at the same density, linking length and halo
-statistics), on the host cores.
+statistics), on the host cores (labels on all of them).
 """
 from __future__ import annotations
 
@@ -166,7 +166,9 @@ def cpu_sample_spec():
     return synth.BoxSpec("fof_128cubed_L125_sample", N, full.L / 8, full.b, nh, full.frac, 0)
 
 
-def time_oracle(spec, reps=1):
+def time_oracle(spec, reps=1, threads=1):
+    """Seconds per run of the oracle on the box: labels (on `threads` threads
+    when > 1: the slab-decomposed oracle), then groups and properties."""
     import numpy as np
 
     import oracle
@@ -177,11 +179,29 @@ def time_oracle(spec, reps=1):
     times = []
     for _ in range(reps):
         t0 = time.perf_counter()
-        lab = oracle.fof_labels(pos_np, spec.L, spec.b)
+        if threads > 1:
+            lab = oracle.fof_labels_mt(pos_np, spec.L, spec.b, threads=threads)
+        else:
+            lab = oracle.fof_labels(pos_np, spec.L, spec.b)
         hid, cnt = oracle.groups(lab, spec.min_size)
         oracle.halo_props(pos64, vel64, hid, len(cnt), spec.L)
         times.append(time.perf_counter() - t0)
     return times
+
+
+def cpu_baseline(spec, reps=3):
+    """The oracle on the host cores: threaded labels (all cores) and, beside
+    it, the single-threaded oracle."""
+    import oracle
+    oracle.build()
+    T = oracle.default_threads()
+    tt = sum(time_oracle(spec, reps, threads=T))
+    t1 = sum(time_oracle(spec, reps, threads=1))
+    return {"value": reps * spec.N / tt, "unit": UNIT, "cores": T, "kind": "oracle",
+            "sample": f"{spec.name}: 128^3-particle box at the 1024^3 box's density, b and halo statistics; "
+                      f"labels on {T} threads (slabs of cell layers), groups + props on one, {reps} runs, "
+                      f"{tt:.1f} s",
+            "single_thread": {"value": reps * spec.N / t1, "cores": 1, "seconds": t1}}
 
 
 def rank_spec(spec, rank: int, world: int):
@@ -214,9 +234,10 @@ def run_reference(args, rank, world):
     spec = cpu_sample_spec()
     oracle_mod = __import__("oracle")
     oracle_mod.build()
+    T = oracle_mod.default_threads()
     for _ in range(args.warmup):
-        time_oracle(spec)
-    ts = [time_oracle(spec)[0] for _ in range(args.steps)]
+        time_oracle(spec, threads=T)
+    ts = [time_oracle(spec, threads=T)[0] for _ in range(args.steps)]
     t = sum(ts)
     value = spec.N * args.steps / t
     line = {
@@ -226,8 +247,8 @@ def run_reference(args, rank, world):
         "impl": "reference",
         "config": {"workload": spec.name, "N": spec.N, "L": spec.L, "b": spec.b,
                    "min_size": spec.min_size, "note": "CPU oracle on a bounded sample of the 1024^3 workload"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{spec.name}: 128^3 particles, labels+groups+props, single thread"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": T, "kind": "oracle",
+                         "sample": f"{spec.name}: 128^3 particles, labels on {T} threads, groups + props on one"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -434,15 +455,9 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
-            spec_s = cpu_sample_spec()
-            __import__("oracle").build()
-            ts = time_oracle(spec_s, reps=3)
-            t = sum(ts)
-            cpu = {"value": 3 * spec_s.N / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"{spec_s.name}: 128^3-particle box at the 1024^3 box's density, b and halo "
-                             f"statistics; labels + groups + props, single thread, 3 runs, {t:.1f} s"}
+            cpu = cpu_baseline(cpu_sample_spec())
         except Exception as e:  # the oracle is a reported baseline, never the product
-            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+            cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": f"failed: {e}"}
 
     extras = {}
     if rank == 0 and not args.no_extras:
