@@ -331,6 +331,62 @@ int jfof_fof_host(jfof_ctx *ctx, const float *h_pos, const float *h_vel, int64_t
                   float *mass, float *com, float *vmean, float *sigv);
 
 /* ---------------------------------------------------------------------- */
+/* Slabs: streaming FoF with bounded device memory (Sec. 2.2, streaming     */
+/* mode) and the slab decomposition with union-find fusion of Sec. 2.3.     */
+/*                                                                          */
+/* The cell grid (n cells per axis, n >= 3) is cut into n_slabs slabs of    */
+/* whole z-layers: slab s owns layers [n s / n_slabs, n (s+1) / n_slabs).    */
+/* A slab's subset is its particles plus those of one more layer on each    */
+/* side (periodic).  Cells are at least 1.01 b wide, so the subset holds    */
+/* every friend of the slab's own particles; linking it in the full         */
+/* periodic box finds only true links, and every link has an end in some    */
+/* slab.  Fusing the slabs' components through the particles that two      */
+/* subsets share gives exactly the FoF groups.  The z layer of a particle   */
+/* is floor(z * f32(n/L)) clamped to [0, n-1], as on the device.            */
+
+/* Host only (no GPU needed).  The subset of slab `slab` of n_slabs:        */
+/* h_pos: HOST float32 [N,3] in [0, L) (JFOF_ERANGE otherwise); n_axis =    */
+/* cells per axis (0 = the default for N, as jfof_fof).  Writes to HOST      */
+/* h_idx[n_sel] the subset's global indices in ascending order and to        */
+/* h_core[n_sel] 1 for the slab's own particles, 0 for the extra layers;    */
+/* either may be NULL (count only).  *n_sel = subset size.  JFOF_EINVAL if   */
+/* n < 3, n_slabs < 1, n_slabs > n or slab is out of range. */
+int jfof_slab_select(const float *h_pos, int64_t N, float L, float b, int32_t n_axis,
+                     int32_t n_slabs, int32_t slab, int64_t *h_idx, uint8_t *h_core,
+                     int64_t *n_sel);
+
+/* Host only.  The union-find fusion of Sec. 2.3 over global indices:       */
+/* classes of [0, N) joined pairwise by (h_a[k], h_b[k]), k < n_pairs (HOST  */
+/* int32), with the smaller index as root; h_label[i] = root of h_pre[i]'s   */
+/* class (HOST int32 [N] in and out; h_pre entries in [0, N)).  With         */
+/* h_pre[i] = particle i's label in its own slab and one pair per particle   */
+/* of an extra layer (its label in its own slab, its label in the other     */
+/* slab), h_label is the smallest index of each FoF group. */
+int jfof_merge_labels(int64_t N, const int32_t *h_pre, int64_t n_pairs, const int32_t *h_a,
+                      const int32_t *h_b, int32_t *h_label);
+
+/* Device workspace bytes for jfof_fof_stream: the largest slab subset's     */
+/* positions, labels and bin/link workspace (reads HOST h_pos to size the    */
+/* subsets). */
+int jfof_fof_stream_bytes(const float *h_pos, int64_t N, float L, float b, int32_t n_axis,
+                          int32_t n_slabs, size_t *bytes);
+
+/* FoF of a box whose positions stay in HOST memory (h_pos, float32 [N,3] in */
+/* [0, L)), slab by slab on the device: each subset is gathered on the host, */
+/* uploaded into ws, binned and linked (the kernels of jfof_bin_cells and    */
+/* jfof_link on the same grid), and its labels copied back; the slabs are   */
+/* then fused as jfof_merge_labels describes.  Device memory is bounded by   */
+/* the largest subset (jfof_fof_stream_bytes) instead of the whole box.      */
+/* Outputs (HOST): h_label[N] raw labels (smallest index of the group),      */
+/* h_halo_id[N] (ascending with the raw label, -1 below min_size; may be     */
+/* NULL), *n_halos (may be NULL).  Synchronises the context's stream once    */
+/* per slab; device errors are returned directly.  Equal to jfof_fof's      */
+/* labels and halo ids for every n_slabs. */
+int jfof_fof_stream(jfof_ctx *ctx, const float *h_pos, int64_t N, float L, float b,
+                    int32_t n_axis, int32_t n_slabs, int32_t min_size, void *ws, size_t ws_bytes,
+                    int32_t *h_label, int32_t *h_halo_id, int64_t *n_halos);
+
+/* ---------------------------------------------------------------------- */
 /* No-allocation variant (the paper has no counterpart).                   */
 
 /* jfof_fof without a workspace argument, for callers that must not allocate

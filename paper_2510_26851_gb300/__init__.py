@@ -31,7 +31,8 @@ EXPORTED = [
     "jfof_prob_coef", "jfof_pairs_bytes", "jfof_pairs", "jfof_reinforce_sample_bytes",
     "jfof_reinforce_sample", "jfof_reinforce_grad_bytes", "jfof_reinforce_grad", "jfof_eval_exp",
     "jfof_eval_edge_uniform", "jfof_batch_bytes", "jfof_fof_batched", "jfof_autotune",
-    "jfof_fof_static", "jfof_fof_host",
+    "jfof_fof_static", "jfof_fof_host", "jfof_slab_select", "jfof_merge_labels", "jfof_fof_stream_bytes",
+    "jfof_fof_stream",
 ]
 
 
@@ -97,6 +98,10 @@ def _declare(lib):
         "jfof_fof_static": [vp, vp, i64, f32, f32, i32, u32, i32, vp, vp, vp, vp, vp, vp],
         "jfof_fof_host": [vp, vp, vp, i64, f32, f32, i32, u32, i32, f32, vp, vp, vp, sz, vp, vp, vp, vp, vp,
                           vp, vp, vp, vp, vp],
+        "jfof_slab_select": [vp, i64, f32, f32, i32, i32, i32, vp, vp, P(i64)],
+        "jfof_merge_labels": [i64, vp, i64, vp, vp, vp],
+        "jfof_fof_stream_bytes": [vp, i64, f32, f32, i32, i32, P(sz)],
+        "jfof_fof_stream": [vp, vp, i64, f32, f32, i32, i32, i32, vp, sz, vp, vp, P(i64)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -663,3 +668,138 @@ def fof_static(pos: torch.Tensor, L: float, b: float, min_size: int = 20, n_axis
                                      _ptr(g.halo_start), _ptr(g.members), _ptr(g.n_halos_dev)),
            "jfof_fof_static")
     return FofResult(label, g, n)
+
+
+# ---------------------------------------------------------------------------
+# Slabs of cell layers: streaming FoF with bounded device memory and the
+# union-find fusion of slabs (include/jfof.h).  Host arrays are CPU tensors.
+
+def _host(t, dtype, name):
+    if t.device.type != "cpu" or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CPU {dtype} tensor")
+    return t
+
+
+def slab_select(h_pos: torch.Tensor, L: float, b: float, n_slabs: int, slab: int, n_axis: int = 0):
+    """Host only: ascending global indices (int64) of slab ``slab``'s subset
+    (its cell layers plus one layer on each side) and its core flags (uint8)."""
+    _host(h_pos, torch.float32, "h_pos")
+    N = h_pos.shape[0]
+    lib = library()
+    cnt = ctypes.c_int64()
+    _check(lib.jfof_slab_select(_ptr(h_pos), N, L, b, n_axis, n_slabs, slab, None, None, ctypes.byref(cnt)),
+           "jfof_slab_select")
+    idx = torch.empty(cnt.value, dtype=torch.int64)
+    core = torch.empty(cnt.value, dtype=torch.uint8)
+    _check(lib.jfof_slab_select(_ptr(h_pos), N, L, b, n_axis, n_slabs, slab, _ptr(idx), _ptr(core),
+                                ctypes.byref(cnt)), "jfof_slab_select")
+    return idx, core
+
+
+def merge_labels(pre: torch.Tensor, a: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
+    """Host only: union-find fusion over global indices (smaller index wins):
+    classes joined pairwise by (a[k], b[k]); returns the root of pre[i]."""
+    for t, nm in ((pre, "pre"), (a, "a"), (b, "b")):
+        _host(t, torch.int32, nm)
+    if a.numel() != b.numel():
+        raise ValueError("a and b must have the same length")
+    out = torch.empty_like(pre)
+    _check(library().jfof_merge_labels(pre.numel(), _ptr(pre), a.numel(), _ptr(a) if a.numel() else None,
+                                       _ptr(b) if b.numel() else None, _ptr(out)), "jfof_merge_labels")
+    return out
+
+
+def fof_stream(h_pos: torch.Tensor, L: float, b: float, n_slabs: int, min_size: int = 20, n_axis: int = 0,
+               device=None):
+    """FoF of positions kept in host memory, one slab of cell layers at a
+    time on the GPU: returns host (label, halo_id, n_halos), equal to
+    :func:`fof`'s labels and halo ids."""
+    _host(h_pos, torch.float32, "h_pos")
+    N = h_pos.shape[0]
+    lib = library()
+    nb = ctypes.c_size_t()
+    _check(lib.jfof_fof_stream_bytes(_ptr(h_pos), N, L, b, n_axis, n_slabs, ctypes.byref(nb)),
+           "jfof_fof_stream_bytes")
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else torch.device(device).index)
+    ws = _ws(nb.value, dev)
+    label = torch.empty(N, dtype=torch.int32)
+    hid = torch.empty(N, dtype=torch.int32)
+    nh = ctypes.c_int64()
+    _check(lib.jfof_fof_stream(context(dev), _ptr(h_pos), N, L, b, n_axis, n_slabs, min_size, _ptr(ws), ws.numel(),
+                               _ptr(label), _ptr(hid), ctypes.byref(nh)), "jfof_fof_stream")
+    return label, hid, nh.value
+
+
+def _link_slab_on_gpu(pos_s: torch.Tensor, L: float, b: float, n_axis: int) -> torch.Tensor:
+    """Raw labels of one slab subset (host positions in, host labels out):
+    jfof_bin_cells + jfof_link on the current GPU with the box's grid."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    grid = bin_cells(pos_s.to(dev), L, b, n_axis=n_axis)
+    lab = link(grid)
+    sync(dev)
+    return lab.cpu()
+
+
+def fof_slabs(h_pos: torch.Tensor, L: float, b: float, min_size: int = 20, n_axis: int = 0, group=None,
+              link_slab=None):
+    """Slab decomposition with union-find fusion over the ranks of a
+    torch.distributed group (Sec. 2.3): rank r of W links slab r of W (its
+    cell layers plus one layer on each side) on its own GPU; the ranks then
+    exchange the labels of the particles two slabs share (two all-gathers of
+    small records) and fuse them with :func:`merge_labels`.  Every rank holds
+    the host positions.  Returns, for this rank's own particles, their global
+    indices (int64), raw labels (smallest index of the group) and halo ids
+    (ascending with the raw label, -1 below min_size), all on the host, and
+    the number of halos.  ``link_slab(pos_s, L, b, n) -> labels`` replaces the
+    GPU link of a slab (the CPU tests pass the oracle)."""
+    import torch.distributed as dist
+
+    _host(h_pos, torch.float32, "h_pos")
+    N = h_pos.shape[0]
+    W = dist.get_world_size(group) if dist.is_initialized() else 1
+    r = dist.get_rank(group) if dist.is_initialized() else 0
+    n = default_cells_per_axis(N, L, b) if n_axis == 0 else int(n_axis)
+    idx, core = slab_select(h_pos, L, b, W, r, n_axis=n)
+    linker = link_slab or _link_slab_on_gpu
+    lab = linker(h_pos[idx].contiguous(), L, b, n).to(torch.int64) if idx.numel() else torch.empty(0, dtype=torch.int64)
+    R = idx[lab] if idx.numel() else idx  # global smallest index of each slab component
+    is_core = core.bool()
+    g_own, r_own = idx[is_core], R[is_core]
+    ghosts = (idx[~is_core], R[~is_core])
+
+    def gather(obj):
+        if W == 1:
+            return [obj]
+        out = [None] * W
+        dist.all_gather_object(out, obj, group=group)
+        return out
+
+    # particles of an extra layer: their label in this slab against their
+    # label in their own slab (known to the rank that owns them)
+    own_label = torch.full((N,), -1, dtype=torch.int64)
+    own_label[g_own] = r_own
+    pa, pb = [], []
+    for gg, rr in gather(ghosts):
+        mine = own_label[gg] >= 0
+        pa.append(own_label[gg][mine])
+        pb.append(rr[mine])
+    pairs = gather((torch.cat(pa) if pa else torch.empty(0, dtype=torch.int64),
+                    torch.cat(pb) if pb else torch.empty(0, dtype=torch.int64)))
+    a = torch.cat([p[0] for p in pairs]).to(torch.int32).contiguous()
+    bb = torch.cat([p[1] for p in pairs]).to(torch.int32).contiguous()
+    pre = torch.arange(N, dtype=torch.int32)
+    pre[g_own] = r_own.to(torch.int32)
+    label = merge_labels(pre, a, bb)[g_own]
+    # groups: counts per raw label over all ranks, the cut, ids ascending
+    u, c = torch.unique(label.to(torch.int64), return_counts=True)
+    parts = gather((u, c))
+    all_u = torch.cat([p[0] for p in parts])
+    all_c = torch.cat([p[1] for p in parts])
+    uu, inv = torch.unique(all_u, return_inverse=True)  # sorted ascending
+    tot = torch.zeros(uu.numel(), dtype=torch.int64).index_add_(0, inv, all_c)
+    kept = uu[tot >= min_size]
+    H = kept.numel()
+    at = torch.searchsorted(kept, label.to(torch.int64))
+    hit = (at < H) & (kept[at.clamp(max=max(H - 1, 0))] == label) if H else torch.zeros_like(at, dtype=torch.bool)
+    halo_id = torch.where(hit, at, torch.full_like(at, -1)).to(torch.int32)
+    return g_own, label, halo_id, H
