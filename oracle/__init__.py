@@ -215,6 +215,75 @@ def halo_props_backward(vel, halo_id, H: int, vmean, sigv, g_com=None, g_vmean=N
     return gp, gv
 
 
+def _declare_decor(lib):
+    c = ctypes
+    lib.orc_halo_decoration.restype = c.c_int
+    lib.orc_halo_decoration.argtypes = [_f64p, _i32p, c.c_int64, c.c_int64, c.c_double, _f64p, _f64p]
+    lib.orc_halo_decoration_backward.restype = c.c_int
+    lib.orc_halo_decoration_backward.argtypes = [_f64p, _i32p, c.c_int64, c.c_int64, c.c_double, _f64p,
+                                                 _f64p, _f64p, _f64p]
+    lib.orc_soft_hist.restype = c.c_int
+    lib.orc_soft_hist.argtypes = [_f64p, c.c_int64, _f64p, c.c_int32, c.c_double, _f64p]
+    lib.orc_soft_hist_backward.restype = c.c_int
+    lib.orc_soft_hist_backward.argtypes = [_f64p, c.c_int64, _f64p, c.c_int32, c.c_double, _f64p, _f64p]
+    return lib
+
+
+def _f64(a, shape=(-1,)):
+    return np.ascontiguousarray(np.asarray(a, np.float64).reshape(shape))
+
+
+def halo_decoration(pos, halo_id, H: int, L: float, com) -> np.ndarray:
+    """FP64 particle standard deviation about each halo's centre (Sec. 3.1.1)."""
+    lib = _declare_decor(_load())
+    p = _f64(pos, (-1, 3))
+    out = np.empty(max(H, 1))
+    st = lib.orc_halo_decoration(p, np.ascontiguousarray(halo_id, np.int32), p.shape[0], H, float(L),
+                                 _f64(com, (-1, 3)) if H else np.zeros((1, 3)), out)
+    if st != 0:
+        raise OracleError(f"orc_halo_decoration status {st}")
+    return out[:H]
+
+
+def halo_decoration_backward(pos, halo_id, H: int, L: float, com, dsig, g_dsig) -> np.ndarray:
+    """FP64 frozen-assignment adjoint of the decoration: g_pos [N,3]."""
+    lib = _declare_decor(_load())
+    p = _f64(pos, (-1, 3))
+    g = np.empty_like(p)
+    z = np.zeros(1)
+    st = lib.orc_halo_decoration_backward(p, np.ascontiguousarray(halo_id, np.int32), p.shape[0], H, float(L),
+                                          _f64(com, (-1, 3)) if H else np.zeros((1, 3)),
+                                          _f64(dsig) if H else z, _f64(g_dsig) if H else z, g)
+    if st != 0:
+        raise OracleError(f"orc_halo_decoration_backward status {st}")
+    return g
+
+
+def soft_hist(ell, edges, width: float) -> np.ndarray:
+    """FP64 soft histogram of the values ell over bins edges[0..B]."""
+    lib = _declare_decor(_load())
+    e = _f64(edges)
+    B = e.size - 1
+    out = np.empty(B)
+    el = _f64(ell) if len(ell) else np.zeros(1)
+    st = lib.orc_soft_hist(el, len(ell), e, B, float(width), out)
+    if st != 0:
+        raise OracleError(f"orc_soft_hist status {st}")
+    return out
+
+
+def soft_hist_backward(ell, edges, width: float, g_hist) -> np.ndarray:
+    """FP64 vector-Jacobian product of :func:`soft_hist` with respect to ell."""
+    lib = _declare_decor(_load())
+    e = _f64(edges)
+    out = np.empty(max(len(ell), 1))
+    st = lib.orc_soft_hist_backward(_f64(ell) if len(ell) else np.zeros(1), len(ell), e, e.size - 1, float(width),
+                                    _f64(g_hist), out)
+    if st != 0:
+        raise OracleError(f"orc_soft_hist_backward status {st}")
+    return out[:len(ell)]
+
+
 def philox4x32_10(ctr, key) -> np.ndarray:
     out = np.empty(4, np.uint32)
     _load().orc_philox4x32_10(np.ascontiguousarray(ctr, np.uint32),

@@ -755,6 +755,108 @@ int orc_halo_props_backward(const double *vel, const int32_t *halo_id, int64_t N
 }
 
 /* ------------------------------------------------------------------------ */
+/* Decorated frozen assignment (Sec. 3.1.1, Eq. 5): a halo "decoration" that  */
+/* is an analytic function of the member positions, here the particle        */
+/* standard deviation about the halo centre,                                 */
+/*   D_h = sqrt( (1/(3 n_h)) sum_i |mi(x_i - X_h)|^2 ),                        */
+/* with X_h the periodic centre of mass (as orc_halo_props), used as a        */
+/* differentiable proxy for the halo mass.  Memberships are frozen.          */
+
+int orc_halo_decoration(const double *pos, const int32_t *halo_id, int64_t N, int64_t H,
+                        double L, const double *com, double *dsig)
+{
+    int64_t *n = (int64_t *)calloc((size_t)(H > 0 ? H : 1), sizeof(int64_t));
+    double *s2 = (double *)calloc((size_t)(H > 0 ? H : 1), sizeof(double));
+    if (!n || !s2) {
+        free(n); free(s2);
+        return ORC_ENOMEM;
+    }
+    for (int64_t i = 0; i < N; ++i) {
+        int32_t h = halo_id[i];
+        if (h < 0)
+            continue;
+        n[h] += 1;
+        for (int a = 0; a < 3; ++a) {
+            double d = mi_f64(pos[3 * i + a] - com[3 * h + a], L);
+            s2[h] += d * d;
+        }
+    }
+    for (int64_t h = 0; h < H; ++h)
+        dsig[h] = sqrt(s2[h] / (3.0 * (double)n[h]));
+    free(n); free(s2);
+    return ORC_OK;
+}
+
+/* Its frozen-assignment adjoint: with d_i = mi(x_i - X_h) and sum_i d_i = 0
+   (X_h is the members' mean), d D_h / d x_i = d_i / (3 n_h D_h), 0 when
+   D_h = 0.  g_pos[i] = g_dsig[h] d D_h / d x_i, 0 outside halos. */
+int orc_halo_decoration_backward(const double *pos, const int32_t *halo_id, int64_t N, int64_t H,
+                                 double L, const double *com, const double *dsig,
+                                 const double *g_dsig, double *g_pos)
+{
+    int64_t *n = (int64_t *)calloc((size_t)(H > 0 ? H : 1), sizeof(int64_t));
+    if (!n)
+        return ORC_ENOMEM;
+    for (int64_t i = 0; i < N; ++i)
+        if (halo_id[i] >= 0)
+            n[halo_id[i]] += 1;
+    for (int64_t i = 0; i < N; ++i) {
+        int32_t h = halo_id[i];
+        for (int a = 0; a < 3; ++a)
+            g_pos[3 * i + a] = 0.0;
+        if (h < 0 || !(dsig[h] > 0.0))
+            continue;
+        double c = g_dsig[h] / (3.0 * (double)n[h] * dsig[h]);
+        for (int a = 0; a < 3; ++a)
+            g_pos[3 * i + a] = c * mi_f64(pos[3 * i + a] - com[3 * h + a], L);
+    }
+    free(n);
+    return ORC_OK;
+}
+
+/* Soft histogram (Sec. 3.1.1: a "soft" histogram so that derivatives flow
+   between bins): bin k of B collects, from every halo h with log-mass
+   ell_h, the weight S((ell_h - e_k)/w) - S((ell_h - e_{k+1})/w), S the
+   logistic function, e[0..B] the bin edges, w > 0 the softness.  As w -> 0
+   it becomes the ordinary histogram. */
+static double logistic(double t)
+{
+    return 1.0 / (1.0 + exp(-t));
+}
+
+int orc_soft_hist(const double *ell, int64_t H, const double *edges, int32_t B, double w,
+                  double *hist)
+{
+    if (B < 1 || !(w > 0.0))
+        return ORC_EINVAL;
+    for (int32_t k = 0; k < B; ++k) {
+        double s = 0.0;
+        for (int64_t h = 0; h < H; ++h)
+            s += logistic((ell[h] - edges[k]) / w) - logistic((ell[h] - edges[k + 1]) / w);
+        hist[k] = s;
+    }
+    return ORC_OK;
+}
+
+/* Its vector-Jacobian product: g_ell[h] = sum_k g_hist[k] (S'(a_k) - S'(a_{k+1})) / w,
+   a_k = (ell_h - e_k)/w, S' = S (1 - S). */
+int orc_soft_hist_backward(const double *ell, int64_t H, const double *edges, int32_t B, double w,
+                           const double *g_hist, double *g_ell)
+{
+    if (B < 1 || !(w > 0.0))
+        return ORC_EINVAL;
+    for (int64_t h = 0; h < H; ++h) {
+        double s = 0.0;
+        for (int32_t k = 0; k < B; ++k) {
+            double s0 = logistic((ell[h] - edges[k]) / w), s1 = logistic((ell[h] - edges[k + 1]) / w);
+            s += g_hist[k] * (s0 * (1.0 - s0) - s1 * (1.0 - s1)) / w;
+        }
+        g_ell[h] = s;
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Counter-based generator: Philox4x32-10 (Salmon, Moraes, Dror & Shaw,      */
 /* "Parallel random numbers: as easy as 1, 2, 3", SC'11).  Round function:   */
 /* two 32x32->64 multiplies by M0, M1, xor with the key, word shuffle; key   */

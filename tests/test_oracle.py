@@ -623,3 +623,109 @@ def test_reinforce_grad_masked_restricts_the_full_gradient():
         gm = oracle.reinforce_grad_masked(pos, spec.L, pi, pj, pp, K, seed, A, form, c, mask)
         assert np.array_equal(gm[inside], full[inside])
         assert not gm[~inside].any()
+
+
+# --------------------------------------------------------------------------
+# Decorated frozen assignment and the soft-histogram mass function
+# (Sec. 3.1.1, Eq. 5): the decoration D_h (particle standard deviation about
+# the halo centre), its adjoint, the soft histogram and its VJP.
+
+def test_decoration_closed_form_across_the_boundary():
+    L, a = 10.0, 0.3
+    c = np.array([0.05, 9.9, 4.0])  # straddles two periodic faces
+    off = np.array([[a, 0, 0], [-a, 0, 0], [0, a, 0], [0, -a, 0], [0, 0, a], [0, 0, -a]])
+    pos = (c + off) % L
+    hid = np.zeros(6, np.int32)
+    _, com, _, _ = oracle.halo_props(pos, np.zeros_like(pos), hid, 1, L)
+    assert np.allclose(com[0], c, atol=1e-12)
+    D = oracle.halo_decoration(pos, hid, 1, L, com)
+    assert abs(D[0] - a / math.sqrt(3.0)) < 1e-12
+
+
+def _decor_box(seed=3):
+    rng = np.random.default_rng(seed)
+    L = 20.0
+    centres = rng.uniform(0, L, (3, 3))
+    centres[0] = [0.1, 19.95, 10.0]  # one halo across the faces
+    sizes = [7, 12, 25]
+    pos = np.concatenate([(cc + rng.normal(0, 0.2, (m, 3))) % L for cc, m in zip(centres, sizes)]
+                         + [rng.uniform(0, L, (10, 3))])
+    hid = np.concatenate([np.full(m, h, np.int32) for h, m in enumerate(sizes)] + [np.full(10, -1, np.int32)])
+    return pos, hid, L, 3
+
+
+def _decor_of(pos, hid, H, L):
+    _, com, _, _ = oracle.halo_props(pos, np.zeros_like(pos), hid, H, L)
+    return oracle.halo_decoration(pos, hid, H, L, com), com
+
+
+def test_decoration_backward_matches_central_differences():
+    # the adjoint drops the centre's dependence on x (its deviations sum to
+    # zero); central differences move the centre too
+    pos, hid, L, H = _decor_box()
+    D, com = _decor_of(pos, hid, H, L)
+    g_dsig = np.array([0.7, -1.3, 2.1])
+    g = oracle.halo_decoration_backward(pos, hid, H, L, com, D, g_dsig)
+    eps = 1e-6
+    fd = np.zeros_like(pos)
+    for i in range(pos.shape[0]):
+        for a in range(3):
+            p1 = pos.copy(); p1[i, a] += eps
+            p0 = pos.copy(); p0[i, a] -= eps
+            fd[i, a] = (g_dsig @ _decor_of(p1, hid, H, L)[0] - g_dsig @ _decor_of(p0, hid, H, L)[0]) / (2 * eps)
+    assert np.allclose(g, fd, rtol=1e-6, atol=1e-8)
+    assert not g[hid < 0].any()
+
+
+def test_soft_hist_limits_and_vjp():
+    rng = np.random.default_rng(4)
+    ell = rng.uniform(1.0, 9.0, 400)
+    edges = np.linspace(0.0, 10.0, 11)
+    ell = ell[np.min(np.abs(ell[:, None] - edges[None, :]), 1) > 1e-3]  # none on an edge
+    hard, _ = np.histogram(ell, bins=edges)
+    assert np.allclose(oracle.soft_hist(ell, edges, 1e-5), hard, atol=1e-9)
+    soft = oracle.soft_hist(ell, edges, 0.3)
+    # the bins telescope: their sum only sees the outer edges
+    S = lambda t: 1.0 / (1.0 + np.exp(-t))
+    assert abs(soft.sum() - (S((ell - edges[0]) / 0.3) - S((ell - edges[-1]) / 0.3)).sum()) < 1e-9
+    g_hist = rng.normal(size=10)
+    g = oracle.soft_hist_backward(ell, edges, 0.3, g_hist)
+    eps = 1e-6
+    for h in range(0, len(ell), 37):
+        e1 = ell.copy(); e1[h] += eps
+        e0 = ell.copy(); e0[h] -= eps
+        fd = (g_hist @ oracle.soft_hist(e1, edges, 0.3) - g_hist @ oracle.soft_hist(e0, edges, 0.3)) / (2 * eps)
+        assert abs(g[h] - fd) < 1e-6 * max(1.0, abs(fd))
+
+
+def surrogate_log_mass(counts, D, D0, kappa, particle_mass=1.0):
+    """Decorated log-mass: log(m_p n_h) in value; its derivative follows the
+    decoration with weight -kappa (sigma as an inverse mass proxy)."""
+    return np.log(particle_mass * np.asarray(counts, np.float64)) - kappa * (np.log(D) - np.log(D0))
+
+
+def test_decorated_mass_function_gradient_chain():
+    # d/dx sum_k g_k H_k(ell(D(x))) with D0 frozen: the chain of the two
+    # adjoints, g_D = -kappa g_ell / D, equals central differences
+    pos, hid, L, H = _decor_box(5)
+    counts = np.bincount(hid[hid >= 0], minlength=H)
+    D0, com = _decor_of(pos, hid, H, L)
+    edges = np.log(np.array([4.0, 8.0, 16.0, 32.0]))
+    kappa, w = 1.5, 0.4
+    g_hist = np.array([0.3, -1.0, 0.8])
+
+    def loss(p):
+        D, _ = _decor_of(p, hid, H, L)
+        return g_hist @ oracle.soft_hist(surrogate_log_mass(counts, D, D0, kappa), edges, w)
+
+    ell = surrogate_log_mass(counts, D0, D0, kappa)
+    g_ell = oracle.soft_hist_backward(ell, edges, w, g_hist)
+    g = oracle.halo_decoration_backward(pos, hid, H, L, com, D0, -kappa * g_ell / D0)
+    eps = 1e-6
+    for i in range(0, pos.shape[0], 3):
+        for a in range(3):
+            p1 = pos.copy(); p1[i, a] += eps
+            p0 = pos.copy(); p0[i, a] -= eps
+            fd = (loss(p1) - loss(p0)) / (2 * eps)
+            assert abs(g[i, a] - fd) < 1e-6 * max(1.0, abs(fd)), (i, a)
+    assert np.abs(g).max() > 1e-3
