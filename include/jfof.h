@@ -331,6 +331,52 @@ int jfof_fof_host(jfof_ctx *ctx, const float *h_pos, const float *h_vel, int64_t
                   float *mass, float *com, float *vmean, float *sigv);
 
 /* ---------------------------------------------------------------------- */
+/* Decorated frozen assignment (Sec. 3.1.1, Eq. 5) and the soft mass        */
+/* function.  The decoration is the particle standard deviation about the   */
+/* halo centre, D_h = sqrt(sum_i |mi(x_i - X_h)|^2 / (3 n_h)), an analytic   */
+/* function of the positions used as a proxy for the halo mass (the paper's */
+/* sigma, which falls as the mass grows).  The soft mass function bins the  */
+/* log-masses ell_h = log(particle_mass n_h) with logistic edges: bin k      */
+/* gets S((ell_h - e_k)/w) - S((ell_h - e_{k+1})/w), S(t) = 1/(1 + exp(-t)). */
+/* Its gradient reaches the positions through the decoration: the decorated */
+/* log-mass moves as -kappa log D_h (reading of Eq. 5 with sigma as an      */
+/* inverse proxy), so g_D = -kappa g_ell / D, then the decoration's adjoint. */
+/* Memberships are frozen; results are deterministic run to run.            */
+
+/* D_h for h < *n_halos (device): pos float32 [N,3] (JFOF_WRAP as in         */
+/* jfof_halo_props), the CSR of jfof_groups, com [H_cap,3] from               */
+/* jfof_halo_props.  Writes dsig[H_cap] (entries below *n_halos). */
+int jfof_halo_decoration(jfof_ctx *ctx, const float *pos, int64_t N, float L, uint32_t flags,
+                         const int32_t *halo_start, const int32_t *members, const int32_t *n_halos,
+                         int64_t H_cap, const float *com, float *dsig);
+
+/* Its adjoint: g_pos[i] = g_dsig[h] mi(x_i - X_h) / (3 n_h D_h) for members */
+/* of halo h (0 when D_h = 0), 0 for particles outside halos (halo_id = -1);  */
+/* count [H] are the halo sizes.  g_pos float32 [N,3] (device). */
+int jfof_halo_decoration_backward(jfof_ctx *ctx, const float *pos, const int32_t *halo_id,
+                                  const int32_t *count, int64_t N, float L, uint32_t flags,
+                                  const float *com, const float *dsig, const float *g_dsig,
+                                  float *g_pos);
+
+/* Workspace bytes of jfof_soft_hmf for up to H_cap halos and B bins          */
+/* (1 <= B <= 4096). */
+int jfof_soft_hmf_bytes(int64_t H_cap, int32_t B, size_t *bytes);
+
+/* Soft mass function: hist[k], k < B, over edges[0..B] (device float32,      */
+/* ascending log-mass) with softness width > 0, from the halo sizes count    */
+/* [*n_halos] (device). */
+int jfof_soft_hmf(jfof_ctx *ctx, const int32_t *count, const int32_t *n_halos, int64_t H_cap,
+                  float particle_mass, const float *edges, int32_t B, float width, void *ws,
+                  size_t ws_bytes, float *hist);
+
+/* Its vector-Jacobian product to the decoration: g_dsig[h] = -kappa g_ell_h  */
+/* / D_h, g_ell_h = sum_k g_hist[k] (S'(a_k) - S'(a_{k+1})) / w, a_k =        */
+/* (ell_h - e_k)/w (0 when D_h = 0).  g_dsig [H_cap] (device). */
+int jfof_soft_hmf_backward(jfof_ctx *ctx, const int32_t *count, const int32_t *n_halos, int64_t H_cap,
+                           float particle_mass, const float *dsig, const float *edges, int32_t B,
+                           float width, float kappa, const float *g_hist, float *g_dsig);
+
+/* ---------------------------------------------------------------------- */
 /* Slabs: streaming FoF with bounded device memory (Sec. 2.2, streaming     */
 /* mode) and the slab decomposition with union-find fusion of Sec. 2.3.     */
 /*                                                                          */

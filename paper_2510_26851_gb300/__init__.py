@@ -32,7 +32,8 @@ EXPORTED = [
     "jfof_reinforce_sample", "jfof_reinforce_grad_bytes", "jfof_reinforce_grad", "jfof_eval_exp",
     "jfof_eval_edge_uniform", "jfof_batch_bytes", "jfof_fof_batched", "jfof_autotune",
     "jfof_fof_static", "jfof_fof_host", "jfof_slab_select", "jfof_merge_labels", "jfof_fof_stream_bytes",
-    "jfof_fof_stream",
+    "jfof_fof_stream", "jfof_halo_decoration", "jfof_halo_decoration_backward", "jfof_soft_hmf_bytes",
+    "jfof_soft_hmf", "jfof_soft_hmf_backward",
 ]
 
 
@@ -102,6 +103,11 @@ def _declare(lib):
         "jfof_merge_labels": [i64, vp, i64, vp, vp, vp],
         "jfof_fof_stream_bytes": [vp, i64, f32, f32, i32, i32, P(sz)],
         "jfof_fof_stream": [vp, vp, i64, f32, f32, i32, i32, i32, vp, sz, vp, vp, P(i64)],
+        "jfof_halo_decoration": [vp, vp, i64, f32, u32, vp, vp, vp, i64, vp, vp],
+        "jfof_halo_decoration_backward": [vp, vp, vp, vp, i64, f32, u32, vp, vp, vp, vp],
+        "jfof_soft_hmf_bytes": [i64, i32, P(sz)],
+        "jfof_soft_hmf": [vp, vp, vp, i64, f32, vp, i32, f32, vp, sz, vp],
+        "jfof_soft_hmf_backward": [vp, vp, vp, i64, f32, vp, vp, i32, f32, f32, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -803,3 +809,77 @@ def fof_slabs(h_pos: torch.Tensor, L: float, b: float, min_size: int = 20, n_axi
     hit = (at < H) & (kept[at.clamp(max=max(H - 1, 0))] == label) if H else torch.zeros_like(at, dtype=torch.bool)
     halo_id = torch.where(hit, at, torch.full_like(at, -1)).to(torch.int32)
     return g_own, label, halo_id, H
+
+
+# ---------------------------------------------------------------------------
+# Decorated frozen assignment and the soft mass function (Sec. 3.1.1, Eq. 5).
+
+def halo_decoration(pos: torch.Tensor, L: float, g: Groups, com: torch.Tensor, wrap: bool = False,
+                    out: torch.Tensor | None = None) -> torch.Tensor:
+    """Particle standard deviation about each halo centre, dsig[H_cap]."""
+    _need(pos, torch.float32, None, "pos")
+    dsig = out if out is not None else torch.empty(g.H_cap, dtype=torch.float32, device=pos.device)
+    _check(library().jfof_halo_decoration(context(pos.device), _ptr(pos), pos.shape[0], L,
+                                          JFOF_WRAP if wrap else 0, _ptr(g.halo_start), _ptr(g.members),
+                                          _ptr(g.n_halos_dev), g.H_cap, _ptr(com), _ptr(dsig)),
+           "jfof_halo_decoration")
+    return dsig
+
+
+def halo_decoration_backward(pos: torch.Tensor, L: float, g: Groups, com, dsig, g_dsig, wrap: bool = False):
+    """Frozen-assignment adjoint of the decoration: g_pos [N,3]."""
+    g_pos = torch.empty_like(pos)
+    _check(library().jfof_halo_decoration_backward(context(pos.device), _ptr(pos), _ptr(g.halo_id), _ptr(g.count),
+                                                   pos.shape[0], L, JFOF_WRAP if wrap else 0, _ptr(com),
+                                                   _ptr(dsig), _ptr(g_dsig.contiguous()), _ptr(g_pos)),
+           "jfof_halo_decoration_backward")
+    return g_pos
+
+
+def soft_hmf(g: Groups, edges: torch.Tensor, width: float, particle_mass: float = 1.0) -> torch.Tensor:
+    """Soft histogram of the halo log-masses over ``edges`` (device float32)."""
+    _need(edges, torch.float32, None, "edges")
+    B = edges.numel() - 1
+    nb = ctypes.c_size_t()
+    _check(library().jfof_soft_hmf_bytes(g.H_cap, B, ctypes.byref(nb)), "jfof_soft_hmf_bytes")
+    ws = _ws(nb.value, edges.device)
+    hist = torch.empty(B, dtype=torch.float32, device=edges.device)
+    _check(library().jfof_soft_hmf(context(edges.device), _ptr(g.count), _ptr(g.n_halos_dev), g.H_cap,
+                                   particle_mass, _ptr(edges), B, width, _ptr(ws), ws.numel(), _ptr(hist)),
+           "jfof_soft_hmf")
+    return hist
+
+
+def soft_hmf_backward(g: Groups, dsig, edges, width: float, kappa: float, g_hist, particle_mass: float = 1.0):
+    """VJP of :func:`soft_hmf` to the decoration: g_dsig[H_cap]."""
+    g_dsig = torch.zeros(g.H_cap, dtype=torch.float32, device=edges.device)
+    _check(library().jfof_soft_hmf_backward(context(edges.device), _ptr(g.count), _ptr(g.n_halos_dev), g.H_cap,
+                                            particle_mass, _ptr(dsig), _ptr(edges), edges.numel() - 1, width,
+                                            kappa, _ptr(g_hist.contiguous()), _ptr(g_dsig)),
+           "jfof_soft_hmf_backward")
+    return g_dsig
+
+
+class DecoratedHMF(torch.autograd.Function):
+    """Soft halo mass function whose gradient reaches the positions through the
+    decoration (decorated frozen assignment, Sec. 3.1.1): forward = soft
+    histogram of log(m_p n_h); backward = its VJP, g_D = -kappa g_ell / D,
+    then the decoration's adjoint.  Memberships are frozen (``g`` from
+    :func:`groups` or :func:`fof`)."""
+
+    @staticmethod
+    def forward(ctx, pos, g: Groups, L: float, edges, width: float, kappa: float = 1.0,
+                particle_mass: float = 1.0, wrap: bool = False):
+        p = halo_props(pos.detach(), None, L, g, particle_mass=particle_mass, wrap=wrap)
+        dsig = halo_decoration(pos.detach(), L, g, p.com, wrap=wrap)
+        hist = soft_hmf(g, edges, width, particle_mass)
+        ctx.save_for_backward(pos.detach(), p.com, dsig, edges)
+        ctx.g, ctx.L, ctx.width, ctx.kappa, ctx.mp, ctx.wrap = g, L, width, kappa, particle_mass, wrap
+        return hist
+
+    @staticmethod
+    def backward(ctx, g_hist):
+        pos, com, dsig, edges = ctx.saved_tensors
+        g_dsig = soft_hmf_backward(ctx.g, dsig, edges, ctx.width, ctx.kappa, g_hist.float(), ctx.mp)
+        g_pos = halo_decoration_backward(pos, ctx.L, ctx.g, com, dsig, g_dsig, wrap=ctx.wrap)
+        return g_pos, None, None, None, None, None, None, None
