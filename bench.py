@@ -266,8 +266,15 @@ def _events_ms(fn, reps):
     return a.elapsed_time(b) / reps
 
 
-def measure_batched(J, reps=3):
-    """64 uneven boxes: one CUDA-graph launch vs the per-box loop."""
+# Algorithmic bytes of the a1-a7 pipeline per particle (the plain path's
+# kernels, each counted once): bin 12 + 28, brick sort 32, link 24, roots 16,
+# labels 16, group count 12, members 8.
+A17_BYTES_PER_PARTICLE = 12 + 28 + 32 + 24 + 16 + 16 + 12 + 8
+
+
+def measure_batched(J, peak, reps=3):
+    """64 uneven boxes: one CUDA-graph launch vs the per-box loop, with the
+    default and the autotuned (grid, cell classes, CTA shape) choices."""
     specs = synth.batch_specs()
     parts = [synth.generate(sp, device="cuda", velocities=False)[0] for sp in specs]
     pos = torch.cat(parts).contiguous()
@@ -283,13 +290,35 @@ def measure_batched(J, reps=3):
     l_ms = _events_ms(lambda: bt.run(pos, use_graph=False), reps)
     J.sync()
     N = int(off[-1])
+    t0 = time.perf_counter()
+    bt2, picks = J.Batch.tuned(pos, off, [s.L for s in specs], [s.b for s in specs], min_size=20, reps=1)
+    tune_s = time.perf_counter() - t0
+    for _ in range(2):
+        bt2.run(pos, use_graph=True)
+        bt2.run(pos, use_graph=False)
+    J.sync()
+    gt_ms = _events_ms(lambda: bt2.run(pos, use_graph=True), reps)
+    lt_ms = _events_ms(lambda: bt2.run(pos, use_graph=False), reps)
+    J.sync()
+    n0 = [J.default_cells_per_axis(sp.N, sp.L, sp.b) for sp in specs]
+    choices = {}
+    for p, d in zip(picks, n0):
+        key = f"n/n0={p[0] / d:.2f} S={p[1]} T={p[2]} shape={p[3]}"
+        choices[key] = choices.get(key, 0) + 1
+    achieved = A17_BYTES_PER_PARTICLE * N / (gt_ms * 1e-3) / 1e9
     return {"workload": "64 boxes, N log-uniform in [32^3, 192^3], L in [50, 400], seeds 0-63",
             "particles": N, "graph_ms": g_ms, "loop_ms": l_ms, "speedup_vs_loop": l_ms / g_ms,
-            "value": N / (g_ms * 1e-3), "unit": UNIT}
+            "tuned": {"graph_ms": gt_ms, "loop_ms": lt_ms, "speedup_vs_loop": l_ms / gt_ms,
+                      "speedup_vs_untuned_graph": g_ms / gt_ms, "tuning_s": tune_s, "choices": choices},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak,
+                         "algorithmic_bytes": f"{A17_BYTES_PER_PARTICLE} B/particle (a1-a7)"},
+            "value": N / (min(g_ms, gt_ms) * 1e-3), "unit": UNIT}
 
 
-def measure_differentiable(J, reps=3):
-    """128^3 box: frozen-assignment forward/backward props and REINFORCE."""
+def measure_differentiable(J, peak, reps=3):
+    """128^3 box: frozen-assignment forward/backward props, the decorated
+    mass function and REINFORCE."""
     spec = synth.DIFF_128
     pos, vel = synth.generate(spec, device="cuda")
     r = J.fof(pos, spec.L, spec.b, spec.min_size)
@@ -304,6 +333,16 @@ def measure_differentiable(J, reps=3):
     fwd = _events_ms(lambda: J.halo_props(pos, vel, spec.L, r.groups, out=p), reps)
     bwd = _events_ms(lambda: J.halo_props_backward(vel, r.groups, p.vmean, p.sigv, g_com=g_com, g_sigv=g_sig),
                      reps)
+    # decorated frozen assignment: decoration + soft mass function, and back
+    import numpy as np
+    edges = torch.from_numpy(np.linspace(np.log(20.0), np.log(3000.0), 17).astype(np.float32)).cuda()
+    com = p.com
+    t_dec = _events_ms(lambda: (J.halo_decoration(pos, spec.L, r.groups, com), J.soft_hmf(r.groups, edges, 0.1)),
+                       reps)
+    dsig = J.halo_decoration(pos, spec.L, r.groups, com)
+    g_hist = torch.ones(16, device="cuda")
+    t_decb = _events_ms(lambda: J.halo_decoration_backward(
+        pos, spec.L, r.groups, com, dsig, J.soft_hmf_backward(r.groups, dsig, edges, 0.1, 1.0, g_hist)), reps)
     pr = J.pairs(pos, spec.L, spec.b)
     K = 256
     labels = torch.empty(K, spec.N, dtype=torch.int32, device="cuda")
@@ -313,10 +352,27 @@ def measure_differentiable(J, reps=3):
     adv = (nh.float() - nh.float().mean()).contiguous()
     t_grad = _events_ms(lambda: J.reinforce_grad(pos, pr, K, 0, adv), reps)
     J.sync()
+    N, E = spec.N, pr.E
+    M = int(r.groups.halo_start[H].item())
+
+    def roof(nbytes, ms, what):
+        a = nbytes / (ms * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak,
+                "algorithmic_bytes": what}
+
     return {"workload": "128^3 box, L=200, b=0.3125", "halos": H,
             "props_fwd_ms": fwd, "props_bwd_ms": bwd, "bwd_over_fwd": bwd / fwd,
-            "reinforce": {"pairs": pr.E, "K": K, "pairs_ms": t_pairs, "sample_ms": t_samp,
-                          "grad_ms": t_grad, "samples_per_s": K / (t_samp * 1e-3)}}
+            "decorated_hmf": {"fwd_ms": t_dec, "bwd_ms": t_decb, "bins": 16},
+            "reinforce": {"pairs": E, "K": K, "pairs_ms": t_pairs, "sample_ms": t_samp,
+                          "grad_ms": t_grad, "samples_per_s": K / (t_samp * 1e-3),
+                          "sample_launches": "one CUDA graph for all K",
+                          "roofline": {
+                              "pairs": roof(16 * N + 16 * E, t_pairs, "pos 16 B/particle + (i, j, d, p) 16 B/pair"),
+                              "samples": roof(12 * E + 4 * K * N, t_samp,
+                                              "pair list (i, j, p) 12 B/pair + labels K N 4 B"),
+                              "grad": roof(16 * E + 24 * N, t_grad,
+                                           "pair list 16 B/pair + pos read, g_pos write 24 B/particle")}},
+            "props_roofline": roof(28 * M, fwd, "member 4 + pos 12 + vel 12 B per member (128^3)")}
 
 
 def main():
@@ -409,6 +465,18 @@ def main():
                 "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": algo_bytes, "launch_ms": per_launch_ms}
     kernels = {k: {"launches": c, "ms_per_step": t / args.steps} for k, (c, t) in trace.items()}
+    # every kernel against the same peak: its algorithmic bytes over its
+    # CUDA-event time (the link counted as one kernel)
+    for k, (c, t) in grouped.items():
+        bpu_k, unit_k = ALGO_BYTES.get(k, (None, None))
+        if bpu_k is None or t <= 0:
+            continue
+        ab = bpu_k * (N if unit_k == "N" else M)
+        if k == "brick_sort":
+            ab += 4 * (-(-n_axis // 16)) ** 3 * 4096
+        a_gbs = ab / ((t / c) * 1e-3) / 1e9
+        kernels.setdefault(k, {"launches": c, "ms_per_step": t / args.steps})
+        kernels[k].update({"algorithmic_gb": ab / 1e9, "achieved_gbs": a_gbs, "frac": a_gbs / peak})
     # a1-a7 alone (labels and groups, without the halo properties): the same
     # timed steps less the property launches' event time
     props_ms = trace.get("halo_props", (0, 0.0))[1] / args.steps
@@ -464,11 +532,11 @@ def main():
         del ws, res, props
         torch.cuda.empty_cache()
         try:
-            extras["batched"] = measure_batched(J)
+            extras["batched"] = measure_batched(J, peak)
         except Exception as e:  # reported, never hidden
             extras["batched"] = {"error": str(e)}
         try:
-            extras["differentiable"] = measure_differentiable(J)
+            extras["differentiable"] = measure_differentiable(J, peak)
         except Exception as e:
             extras["differentiable"] = {"error": str(e)}
 

@@ -19,7 +19,9 @@
  *     argument's comment says "host".  The library never frees caller memory.
  *   - Scratch memory is passed in by the caller as (ws, ws_bytes); the matching
  *     *_bytes query gives the size.  No call allocates device memory except
- *     jfof_create (a few bytes of status words per context).
+ *     jfof_create (a few bytes of status words per context) and the CUDA
+ *     graphs and streams that jfof_fof_batched and jfof_reinforce_sample
+ *     create on first use and keep in the context.
  *   - Work is enqueued on the context's CUDA stream and the call returns without
  *     waiting, except where a comment says the call synchronises.
  *   - Particle indices are int32: N <= 2^31 - 1.  Positions are float32 AoS
@@ -94,6 +96,11 @@ int jfof_trace_read(jfof_ctx *ctx, char *buf, size_t len, size_t *written);
    cell).  Defaults 8 and 96.  Labels do not depend on them; only speed does.
    Takes effect at the next jfof_bin_cells. */
 int jfof_set_cell_classes(jfof_ctx *ctx, int32_t small_max, int32_t dense_over);
+
+/* Tuning knob: warps per CTA of the four list-driven link kernels (medium
+   cells local and cross, dense cells local and neighbours).  Shape 0 (the
+   default) = (4, 8, 4, 8), 1 = all 8, 2 = all 4.  Labels do not depend on it. */
+int jfof_set_cta_shape(jfof_ctx *ctx, int32_t shape);
 
 /* ---------------------------------------------------------------------- */
 /* Grid choice (Sec. 2.2, Algorithm 2 "Grid setup").                        */
@@ -237,7 +244,10 @@ int jfof_pairs(jfof_ctx *ctx, const float *pos, int64_t N, float L, float b, flo
    (min(i,j), max(i,j), floor(k/4), 0).  Outputs: labels [K, N] device int32,
    row k = smallest member index of each particle's component in sample k;
    n_halos [K] device int32 = components with >= min_size members.  E is the
-   host pair count.  The pair arrays are from jfof_pairs. */
+   host pair count.  The pair arrays are from jfof_pairs.  All K samples run
+   as ONE CUDA graph launch on the context's stream (chunks of 16 samples,
+   so a chunk's label rows stay in L2); the graph is kept in the context and
+   updated in place by later calls of the same shape. */
 int jfof_reinforce_sample_bytes(int64_t N, size_t *bytes);
 int jfof_reinforce_sample(jfof_ctx *ctx, int64_t N, const int32_t *pair_i, const int32_t *pair_j,
                           const float *pair_p, int64_t E, int32_t K, uint64_t seed,
@@ -280,8 +290,9 @@ int jfof_batch_bytes(const int64_t *h_box_offset, int32_t B, const float *h_L, c
 /* a1-a7 for B boxes: labels (smallest member index, numbered inside each
    box), halo ids (numbered from 0 inside each box, -1 below min_size) and
    n_halos [B], all device arrays over the concatenated particles.  Boxes
-   never interact.  h_small / h_dense: host [B] per-box cell classes (NULL =
-   the context's).  use_graph != 0: the first call captures every box's
+   never interact.  h_small / h_dense: host [B] per-box cell classes, h_shape:
+   host [B] per-box CTA shapes of the link kernels (jfof_set_cta_shape), each
+   NULL = the context's; per-box choices come from jfof_autotune.  use_graph != 0: the first call captures every box's
    pipeline as a parallel branch of one CUDA graph and later calls with the
    same configuration (pointers, sizes, parameters, stream) replay it with a
    single launch; use_graph = 0 enqueues the boxes one after another (the
@@ -289,19 +300,24 @@ int jfof_batch_bytes(const int64_t *h_box_offset, int32_t B, const float *h_L, c
    being captured. */
 int jfof_fof_batched(jfof_ctx *ctx, const float *pos, const int64_t *h_box_offset, int32_t B,
                      const float *h_L, const float *h_b, const int32_t *h_n_axis,
-                     const int32_t *h_small, const int32_t *h_dense, uint32_t flags,
-                     int32_t min_size, void *ws, size_t ws_bytes, int32_t *label,
+                     const int32_t *h_small, const int32_t *h_dense, const int32_t *h_shape,
+                     uint32_t flags, int32_t min_size, void *ws, size_t ws_bytes, int32_t *label,
                      int32_t *halo_id, int32_t *n_halos, int32_t use_graph);
 
 /* Autotuner: times the a1-a7 pipeline on one box for candidate grids (the
-   default n and n scaled by 0.8 and 1.26, where the workspace fits) and cell
-   classes, `reps` runs each after a warm-up, and returns the fastest choice
-   (*best_n_axis, *best_small, *best_dense) and its time in ms.  Synchronises.
-   Outputs label/halo_id [N] and n_halos [1] are scratch for the trials. */
+   default n and n scaled by 0.8 and 1.26, where the workspace fits) and six
+   cell-class pairs with the default CTA shape, then the other CTA shapes for
+   the best of those, `reps` runs each after a warm-up, and returns the
+   fastest choice (*best_n_axis, *best_small, *best_dense, *best_shape) and
+   its time in ms.  The choice is kept in the context by size bucket
+   (round(2 log2 N), round(4 log2(L/b))); use_cache != 0 returns a kept choice
+   for the same bucket without timing.  Synchronises.  Outputs label/halo_id
+   [N] and n_halos [1] are scratch for the trials.  Labels never depend on
+   the choice. */
 int jfof_autotune(jfof_ctx *ctx, const float *pos, int64_t N, float L, float b, uint32_t flags,
                   int32_t min_size, void *ws, size_t ws_bytes, int32_t *label, int32_t *halo_id,
-                  int32_t *n_halos, int32_t reps, int32_t *best_n_axis, int32_t *best_small,
-                  int32_t *best_dense, float *best_ms);
+                  int32_t *n_halos, int32_t reps, int32_t use_cache, int32_t *best_n_axis,
+                  int32_t *best_small, int32_t *best_dense, int32_t *best_shape, float *best_ms);
 
 /* Convenience: a1-a7 in one call (bin, link, groups) with one workspace. */
 int jfof_fof_all_bytes(int64_t N, int32_t n_axis, size_t *bytes);

@@ -25,7 +25,7 @@ JFOF_WRAP = 1
 # Every symbol the header declares (checked by the tests).
 EXPORTED = [
     "jfof_create", "jfof_destroy", "jfof_set_stream", "jfof_sync", "jfof_strerror",
-    "jfof_set_loop_budget", "jfof_set_cell_classes", "jfof_trace_enable", "jfof_trace_read", "jfof_max_cells_per_axis", "jfof_default_cells_per_axis",
+    "jfof_set_loop_budget", "jfof_set_cell_classes", "jfof_set_cta_shape", "jfof_trace_enable", "jfof_trace_read", "jfof_max_cells_per_axis", "jfof_default_cells_per_axis",
     "jfof_fof_bytes", "jfof_bin_cells", "jfof_link", "jfof_groups_bytes", "jfof_groups",
     "jfof_halo_props", "jfof_halo_props_backward", "jfof_fof_all_bytes", "jfof_fof",
     "jfof_prob_coef", "jfof_pairs_bytes", "jfof_pairs", "jfof_reinforce_sample_bytes",
@@ -69,6 +69,7 @@ def _declare(lib):
         "jfof_sync": [vp],
         "jfof_set_loop_budget": [vp, i64],
         "jfof_set_cell_classes": [vp, i32, i32],
+        "jfof_set_cta_shape": [vp, i32],
         "jfof_trace_enable": [vp, c.c_int],
         "jfof_trace_read": [vp, c.c_char_p, sz, P(sz)],
         "jfof_max_cells_per_axis": [f32, f32, P(i32)],
@@ -93,9 +94,9 @@ def _declare(lib):
         "jfof_eval_exp": [vp, vp, vp, i64],
         "jfof_eval_edge_uniform": [vp, c.c_uint64, vp, vp, vp, vp, i64],
         "jfof_batch_bytes": [vp, i32, vp, vp, vp, i32, P(sz)],
-        "jfof_fof_batched": [vp, vp, vp, i32, vp, vp, vp, vp, vp, u32, i32, vp, sz, vp, vp, vp, i32],
-        "jfof_autotune": [vp, vp, i64, f32, f32, u32, i32, vp, sz, vp, vp, vp, i32, P(i32), P(i32),
-                          P(i32), P(f32)],
+        "jfof_fof_batched": [vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, u32, i32, vp, sz, vp, vp, vp, i32],
+        "jfof_autotune": [vp, vp, i64, f32, f32, u32, i32, vp, sz, vp, vp, vp, i32, i32, P(i32), P(i32),
+                          P(i32), P(i32), P(f32)],
         "jfof_fof_static": [vp, vp, i64, f32, f32, i32, u32, i32, vp, vp, vp, vp, vp, vp],
         "jfof_fof_host": [vp, vp, vp, i64, f32, f32, i32, u32, i32, f32, vp, vp, vp, sz, vp, vp, vp, vp, vp,
                           vp, vp, vp, vp, vp],
@@ -600,7 +601,7 @@ class Batch:
     concatenated particles."""
 
     def __init__(self, box_offset, L, b, min_size: int = 20, n_axis=None, small=None, dense=None,
-                 device=None):
+                 shape=None, device=None):
         import numpy as _np
         self.off = _np.ascontiguousarray(box_offset, _np.int64)
         self.B = len(self.off) - 1
@@ -609,6 +610,7 @@ class Batch:
         self.n = None if n_axis is None else _np.ascontiguousarray(n_axis, _np.int32)
         self.small = None if small is None else _np.ascontiguousarray(small, _np.int32)
         self.dense = None if dense is None else _np.ascontiguousarray(dense, _np.int32)
+        self.shape = None if shape is None else _np.ascontiguousarray(shape, _np.int32)
         self.min_size = min_size
         dev = torch.device("cuda") if device is None else torch.device(device)
         s = ctypes.c_size_t()
@@ -626,15 +628,39 @@ class Batch:
         arr = lambda a: None if a is None else a.ctypes.data  # noqa: E731
         _check(library().jfof_fof_batched(
             context(pos.device), _ptr(pos), self.off.ctypes.data, self.B, self.L.ctypes.data,
-            self.b.ctypes.data, arr(self.n), arr(self.small), arr(self.dense), JFOF_WRAP if wrap else 0,
+            self.b.ctypes.data, arr(self.n), arr(self.small), arr(self.dense), arr(self.shape),
+            JFOF_WRAP if wrap else 0,
             self.min_size, _ptr(self.ws), self.ws.numel(), _ptr(self.label), _ptr(self.halo_id),
             _ptr(self.n_halos), 1 if use_graph else 0), "jfof_fof_batched")
         return self.label, self.halo_id, self.n_halos
 
+    @classmethod
+    def tuned(cls, pos: torch.Tensor, box_offset, L, b, min_size: int = 20, reps: int = 2, use_cache: bool = True,
+              wrap: bool = False):
+        """A batch whose boxes each run with the autotuner's choice of grid,
+        cell classes and CTA shape (boxes of one size bucket share a choice
+        through the context's cache).  Returns (batch, per-box choices)."""
+        import numpy as _np
+        off = _np.ascontiguousarray(box_offset, _np.int64)
+        picks = []
+        for k in range(len(off) - 1):
+            sl = pos[int(off[k]):int(off[k + 1])]
+            picks.append(autotune(sl, float(L[k]), float(b[k]), min_size, reps=reps, wrap=wrap,
+                                  use_cache=use_cache))
+        n, S, T, W = (list(c) for c in zip(*[p[:4] for p in picks]))
+        return cls(off, L, b, min_size, n_axis=n, small=S, dense=T, shape=W, device=pos.device), picks
+
+
+def set_cta_shape(shape: int = 0, device=None):
+    """CTA shape of the list-driven link kernels: 0 = (4, 8, 4, 8) warps, 1 = all 8, 2 = all 4."""
+    _check(library().jfof_set_cta_shape(context(device), shape), "jfof_set_cta_shape")
+
 
 def autotune(pos: torch.Tensor, L: float, b: float, min_size: int = 20, reps: int = 2,
-             wrap: bool = False):
-    """Fastest (n_axis, small, dense, ms) for this box among the candidates."""
+             wrap: bool = False, use_cache: bool = False):
+    """Fastest (n_axis, small, dense, cta_shape, ms) for this box among the
+    candidates; ``use_cache`` returns a choice already made for the same size
+    bucket without timing."""
     _need(pos, torch.float32, None, "pos")
     N = pos.shape[0]
     dev = pos.device
@@ -646,12 +672,12 @@ def autotune(pos: torch.Tensor, L: float, b: float, min_size: int = 20, reps: in
     label = torch.empty(N, dtype=torch.int32, device=dev)
     hid = torch.empty(N, dtype=torch.int32, device=dev)
     nh = torch.empty(1, dtype=torch.int32, device=dev)
-    bn, bs, bd, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    bn, bs, bd, bw, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
     _check(library().jfof_autotune(context(dev), _ptr(pos), N, L, b, JFOF_WRAP if wrap else 0, min_size,
                                    _ptr(ws), ws.numel(), _ptr(label), _ptr(hid), _ptr(nh), reps,
-                                   ctypes.byref(bn), ctypes.byref(bs), ctypes.byref(bd), ctypes.byref(ms)),
-           "jfof_autotune")
-    return bn.value, bs.value, bd.value, ms.value
+                                   1 if use_cache else 0, ctypes.byref(bn), ctypes.byref(bs), ctypes.byref(bd),
+                                   ctypes.byref(bw), ctypes.byref(ms)), "jfof_autotune")
+    return bn.value, bs.value, bd.value, bw.value, ms.value
 
 
 def fof_static(pos: torch.Tensor, L: float, b: float, min_size: int = 20, n_axis: int = 0,

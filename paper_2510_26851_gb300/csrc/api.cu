@@ -151,9 +151,13 @@ int jfof_create(jfof_ctx **ctx, int device, void *stream) {
     c->loop_budget = kDefaultLoopBudget;
     c->dense_threshold = kDefaultDenseThreshold;
     c->small_threshold = kDefaultSmallThreshold;
+    c->cta_shape = 0;
+    c->tune = nullptr;
     c->copy_stream = nullptr;
     c->ev_pos = nullptr;
     c->ev_vel = nullptr;
+    c->cap_stream = nullptr;
+    c->sample_exec = nullptr;
     if (cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess) {
         delete c;
         return JFOF_ECUDA;
@@ -180,12 +184,15 @@ int jfof_destroy(jfof_ctx *ctx) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     destroy_batch_cache(ctx->batch);
+    destroy_tune_cache(ctx->tune);
     if (ctx->copy_stream) {
         cudaStreamSynchronize(ctx->copy_stream);
         cudaEventDestroy(ctx->ev_pos);
         cudaEventDestroy(ctx->ev_vel);
         cudaStreamDestroy(ctx->copy_stream);
     }
+    if (ctx->sample_exec) cudaGraphExecDestroy(ctx->sample_exec);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     cudaFree(ctx->d_status);
     cudaFreeHost(ctx->h_status);
     delete ctx;
@@ -247,7 +254,7 @@ int jfof_bin_cells(jfof_ctx *ctx, const float *pos, int64_t N, float L, float b,
     if (ws_bytes < need) return JFOF_ENOMEM;
     cudaSetDevice(ctx->device);
     CtxScope scope(ctx);
-    LinkParams lp = make_link_params(N, L, b, n, ctx->small_threshold, ctx->dense_threshold);
+    LinkParams lp = make_link_params(N, L, b, n, ctx->small_threshold, ctx->dense_threshold, ctx->cta_shape);
     launch_bin_cells(pos, N, L, n, (flags & JFOF_WRAP) != 0, lp, fb, ctx->dev(), ctx->stream);
     jfof_cells c;
     c.n = N;
@@ -275,12 +282,18 @@ int jfof_link(jfof_ctx *ctx, const jfof_cells *cells, int32_t *label) {
     fof_layout(cells->n, cells->n_axis, &fb, cells->workspace);
     if (fb.spos != cells->spos || fb.cell_start != cells->cell_start) return JFOF_EINVAL;
     LinkParams lp = make_link_params(cells->n, cells->L, cells->b, cells->n_axis, cells->small_threshold,
-                                     cells->dense_threshold);
+                                     cells->dense_threshold, ctx->cta_shape);
     if (lp.T != cells->dense_threshold || lp.S != cells->small_threshold) return JFOF_EINVAL;
     cudaSetDevice(ctx->device);
     CtxScope scope(ctx);
     launch_link(*cells, fb, lp, label, ctx->dev(), ctx->stream);
     return launch_status();
+}
+
+int jfof_set_cta_shape(jfof_ctx *ctx, int32_t shape) {
+    if (!ctx || shape < 0 || shape >= kCtaShapes) return JFOF_EINVAL;
+    ctx->cta_shape = shape;
+    return JFOF_OK;
 }
 
 int jfof_set_cell_classes(jfof_ctx *ctx, int32_t small_max, int32_t dense_over) {
@@ -369,7 +382,7 @@ int jfof_fof(jfof_ctx *ctx, const float *pos, int64_t N, float L, float b, int32
     fof_layout(N, n, &fb, ws);
     GroupBuffers gb;
     groups_layout(N, H_cap, &gb, reinterpret_cast<char *>(ws) + a);
-    LinkParams lp = make_link_params(N, L, b, n, cells.small_threshold, cells.dense_threshold);
+    LinkParams lp = make_link_params(N, L, b, n, cells.small_threshold, cells.dense_threshold, ctx->cta_shape);
     cudaSetDevice(ctx->device);
     CtxScope scope(ctx);
     launch_link_core(cells, fb, lp, ctx->dev(), ctx->stream);

@@ -1,8 +1,12 @@
 // api_batch.cu -- a10: many independent boxes of uneven size in one CUDA-graph
 // launch (each box's bin/link/groups pipeline on its own stream branch, so
 // small boxes and the narrow phases of large ones overlap), the per-box loop
-// it is compared with, and the cell-class autotuner.
+// it is compared with, and the autotuner (grid size, cell classes and CTA
+// shape of the link kernels, with a per-size-bucket cache in the context).
+#include <cmath>
 #include <cstring>
+#include <map>
+#include <utility>
 #include <vector>
 
 #include "jfof_internal.cuh"
@@ -23,13 +27,13 @@ struct BoxPlan {
     size_t count_off, start_off, members_off, total;
 };
 
-static BoxPlan plan_box(int64_t N, float L, float b, int n, int S, int T, int min_size) {
+static BoxPlan plan_box(int64_t N, float L, float b, int n, int S, int T, int shape, int min_size) {
     BoxPlan p{};
     p.N = N;
     p.L = L;
     p.b = b;
     p.n = n;
-    p.lp = make_link_params(N, L, b, n, S, T);
+    p.lp = make_link_params(N, L, b, n, S, T, shape);
     p.H_cap = N / min_size > 0 ? N / min_size : 1;
     p.fof_bytes = fof_layout(N, n, nullptr, nullptr);
     p.grp_bytes = groups_layout(N, p.H_cap, nullptr, nullptr);
@@ -70,7 +74,7 @@ static void run_box(const BoxPlan &p, const float *pos, uint32_t flags, int min_
 struct BatchCache {
     std::vector<int64_t> off;
     std::vector<float> L, b;
-    std::vector<int> n, S, T;
+    std::vector<int> n, S, T, W;
     const void *pos = nullptr, *ws = nullptr, *label = nullptr, *halo_id = nullptr, *n_halos = nullptr;
     uint32_t flags = 0;
     int min_size = 0;
@@ -87,6 +91,18 @@ struct BatchCache {
 
 void destroy_batch_cache(BatchCache *c) { delete c; }
 
+// Autotuner choices by size bucket: (round(2 log2 N), round(4 log2(L/b))).
+struct TuneChoice {
+    double n_ratio;  // chosen n over the default n of the box
+    int S, T, shape;
+    float ms;
+};
+struct TuneCache {
+    std::map<std::pair<int, int>, TuneChoice> best;
+};
+
+void destroy_tune_cache(TuneCache *c) { delete c; }
+
 }  // namespace jfof
 
 namespace {
@@ -98,7 +114,8 @@ struct BatchArgs {
 };
 
 int plan_batch(const int64_t *h_off, int32_t B, const float *h_L, const float *h_b, const int32_t *h_n,
-               const int32_t *h_S, const int32_t *h_T, int S_def, int T_def, int min_size, BatchArgs *out) {
+               const int32_t *h_S, const int32_t *h_T, const int32_t *h_W, int S_def, int T_def, int W_def,
+               int min_size, BatchArgs *out) {
     if (!h_off || B < 1 || !h_L || !h_b || min_size < 1 || h_off[0] != 0) return JFOF_EINVAL;
     out->boxes.clear();
     size_t off = 0;
@@ -108,7 +125,9 @@ int plan_batch(const int64_t *h_off, int32_t B, const float *h_L, const float *h
         if (e) return e;
         int32_t n;
         if ((e = resolve_n(N, h_L[k], h_b[k], h_n ? h_n[k] : 0, &n))) return e;
-        BoxPlan p = plan_box(N, h_L[k], h_b[k], n, h_S ? h_S[k] : S_def, h_T ? h_T[k] : T_def, min_size);
+        const int W = h_W ? h_W[k] : W_def;
+        if (W < 0 || W >= kCtaShapes) return JFOF_EINVAL;
+        BoxPlan p = plan_box(N, h_L[k], h_b[k], n, h_S ? h_S[k] : S_def, h_T ? h_T[k] : T_def, W, min_size);
         p.ws_off = off;
         off += align_up(p.total);
         out->boxes.push_back(p);
@@ -129,7 +148,7 @@ bool same_config(const BatchCache &c, const BatchArgs &a, const int64_t *h_off, 
     for (int k = 0; k < B; ++k) {
         const BoxPlan &p = a.boxes[k];
         if (c.off[k + 1] != h_off[k + 1] || c.L[k] != p.L || c.b[k] != p.b || c.n[k] != p.n || c.S[k] != p.lp.S ||
-            c.T[k] != p.lp.T)
+            c.T[k] != p.lp.T || c.W[k] != p.lp.warps[0] * 100 + p.lp.warps[1] * 10 + p.lp.warps[2])
             return false;
     }
     return true;
@@ -143,7 +162,7 @@ int jfof_batch_bytes(const int64_t *h_box_offset, int32_t B, const float *h_L, c
                      const int32_t *h_n_axis, int32_t min_size, size_t *bytes) {
     if (!bytes) return JFOF_EINVAL;
     BatchArgs a;
-    int e = plan_batch(h_box_offset, B, h_L, h_b, h_n_axis, nullptr, nullptr, 8, 64, min_size, &a);
+    int e = plan_batch(h_box_offset, B, h_L, h_b, h_n_axis, nullptr, nullptr, nullptr, 8, 64, 0, min_size, &a);
     if (e) return e;
     *bytes = a.ws_bytes;
     return JFOF_OK;
@@ -151,12 +170,12 @@ int jfof_batch_bytes(const int64_t *h_box_offset, int32_t B, const float *h_L, c
 
 int jfof_fof_batched(jfof_ctx *ctx, const float *pos, const int64_t *h_box_offset, int32_t B, const float *h_L,
                      const float *h_b, const int32_t *h_n_axis, const int32_t *h_small, const int32_t *h_dense,
-                     uint32_t flags, int32_t min_size, void *ws, size_t ws_bytes, int32_t *label,
-                     int32_t *halo_id, int32_t *n_halos, int32_t use_graph) {
+                     const int32_t *h_shape, uint32_t flags, int32_t min_size, void *ws, size_t ws_bytes,
+                     int32_t *label, int32_t *halo_id, int32_t *n_halos, int32_t use_graph) {
     if (!ctx || !pos || !ws || !label || !halo_id || !n_halos) return JFOF_EINVAL;
     BatchArgs a;
-    int e = plan_batch(h_box_offset, B, h_L, h_b, h_n_axis, h_small, h_dense, ctx->small_threshold,
-                       ctx->dense_threshold, min_size, &a);
+    int e = plan_batch(h_box_offset, B, h_L, h_b, h_n_axis, h_small, h_dense, h_shape, ctx->small_threshold,
+                       ctx->dense_threshold, ctx->cta_shape, min_size, &a);
     if (e) return e;
     if (ws_bytes < a.ws_bytes) return JFOF_ENOMEM;
     cudaSetDevice(ctx->device);
@@ -219,12 +238,14 @@ int jfof_fof_batched(jfof_ctx *ctx, const float *pos, const int64_t *h_box_offse
         c.n.clear();
         c.S.clear();
         c.T.clear();
+        c.W.clear();
         for (auto &p : a.boxes) {
             c.L.push_back(p.L);
             c.b.push_back(p.b);
             c.n.push_back(p.n);
             c.S.push_back(p.lp.S);
             c.T.push_back(p.lp.T);
+            c.W.push_back(p.lp.warps[0] * 100 + p.lp.warps[1] * 10 + p.lp.warps[2]);
         }
         c.pos = pos;
         c.ws = ws;
@@ -238,63 +259,107 @@ int jfof_fof_batched(jfof_ctx *ctx, const float *pos, const int64_t *h_box_offse
     return cudaGraphLaunch(c.exec, ctx->stream) == cudaSuccess ? JFOF_OK : JFOF_ECUDA;
 }
 
-// Autotuner: times jfof_fof-equivalent runs of one box for candidate cell
-// classes (S, T) and grids n (those whose workspace fits ws), `reps` runs
-// each after one warm-up, and returns the fastest.  Synchronises.  Labels do
-// not depend on the choice.
+// Autotuner: times jfof_fof-equivalent runs of one box (one warm-up, then
+// `reps` runs each, CUDA events) over grids n in {n0, 0.8 n0, 1.26 n0}
+// (those whose workspace fits ws) and six cell-class pairs (S, T) with the
+// default CTA shape, then the other CTA shapes of the link kernels for the
+// best of those, and returns the fastest.  The choice is kept in the context
+// by size bucket (round(2 log2 N), round(4 log2(L/b))); with use_cache a box
+// of a known bucket gets it back without timing (*best_ms = the time it was
+// chosen with).  Synchronises.  Labels do not depend on the choice.
 int jfof_autotune(jfof_ctx *ctx, const float *pos, int64_t N, float L, float b, uint32_t flags, int32_t min_size,
                   void *ws, size_t ws_bytes, int32_t *label, int32_t *halo_id, int32_t *n_halos, int32_t reps,
-                  int32_t *best_n_axis, int32_t *best_small, int32_t *best_dense, float *best_ms) {
+                  int32_t use_cache, int32_t *best_n_axis, int32_t *best_small, int32_t *best_dense,
+                  int32_t *best_shape, float *best_ms) {
     if (!ctx || !pos || !ws || !label || !halo_id || !n_halos || !best_n_axis || !best_small || !best_dense ||
-        reps < 1)
+        !best_shape || reps < 1)
         return JFOF_EINVAL;
     int e = check_box(N, L, b);
     if (e) return e;
     int32_t n0;
     if ((e = resolve_n(N, L, b, 0, &n0))) return e;
     int32_t nmax = max_cells(L, b);
+    const std::pair<int, int> key{int(std::lround(2.0 * std::log2(double(N)))),
+                                  int(std::lround(4.0 * std::log2(double(L) / double(b))))};
+    if (!ctx->tune) ctx->tune = new TuneCache();
+    auto legal = [&](int n) { return n >= 3 && n <= nmax; };
+    if (use_cache) {
+        auto it = ctx->tune->best.find(key);
+        if (it != ctx->tune->best.end()) {
+            const TuneChoice &c = it->second;
+            int n = int(std::lround(n0 * c.n_ratio));
+            if (!legal(n)) n = n0;
+            BoxPlan p = plan_box(N, L, b, n, c.S, c.T, c.shape, min_size);
+            if (p.total <= ws_bytes) {
+                *best_n_axis = n;
+                *best_small = c.S;
+                *best_dense = c.T;
+                *best_shape = c.shape;
+                if (best_ms) *best_ms = c.ms;
+                return JFOF_OK;
+            }
+        }
+    }
     std::vector<int> ns = {n0};
     for (double f : {0.8, 1.26}) {
         int n = int(n0 * f);
-        if (n >= 3 && n <= nmax && n != n0) ns.push_back(n);
+        if (legal(n) && n != n0) ns.push_back(n);
     }
     const int cls[][2] = {{8, 96}, {8, 64}, {4, 96}, {8, 128}, {16, 96}, {8, 48}};
     cudaSetDevice(ctx->device);
     cudaEvent_t t0, t1;
-    cudaEventCreate(&t0);
-    cudaEventCreate(&t1);
+    if (cudaEventCreate(&t0) != cudaSuccess) return JFOF_ECUDA;
+    if (cudaEventCreate(&t1) != cudaSuccess) {
+        cudaEventDestroy(t0);
+        return JFOF_ECUDA;
+    }
     float best = 1e30f;
+    int bn = n0, bS = 8, bT = 96, bW = 0;
     DevStatus st = ctx->dev();
-    for (int n : ns) {
-        for (auto &c : cls) {
-            BoxPlan p = plan_box(N, L, b, n, c[0], c[1], min_size);
-            if (p.total > ws_bytes) continue;
+    auto time_one = [&](int n, int S, int T, int W, float *ms) -> int {
+        BoxPlan p = plan_box(N, L, b, n, S, T, W, min_size);
+        if (p.total > ws_bytes) return 1;
+        run_box(p, pos, flags, min_size, reinterpret_cast<char *>(ws), label, halo_id, n_halos, st, ctx->stream);
+        cudaEventRecord(t0, ctx->stream);
+        for (int r = 0; r < reps; ++r)
             run_box(p, pos, flags, min_size, reinterpret_cast<char *>(ws), label, halo_id, n_halos, st, ctx->stream);
-            cudaEventRecord(t0, ctx->stream);
-            for (int r = 0; r < reps; ++r)
-                run_box(p, pos, flags, min_size, reinterpret_cast<char *>(ws), label, halo_id, n_halos, st,
-                        ctx->stream);
-            cudaEventRecord(t1, ctx->stream);
-            if (cudaEventSynchronize(t1) != cudaSuccess) {
-                cudaEventDestroy(t0);
-                cudaEventDestroy(t1);
-                return JFOF_ECUDA;
-            }
+        cudaEventRecord(t1, ctx->stream);
+        if (cudaEventSynchronize(t1) != cudaSuccess) return -1;
+        cudaEventElapsedTime(ms, t0, t1);
+        *ms /= reps;
+        return 0;
+    };
+    int rc = 0;
+    for (int n : ns)
+        for (auto &c : cls) {
             float ms = 0.f;
-            cudaEventElapsedTime(&ms, t0, t1);
-            ms /= reps;
-            if (ms < best) {
+            if ((rc = time_one(n, c[0], c[1], 0, &ms)) < 0) break;
+            if (rc == 0 && ms < best) {
                 best = ms;
-                *best_n_axis = n;
-                *best_small = c[0];
-                *best_dense = c[1];
+                bn = n;
+                bS = c[0];
+                bT = c[1];
             }
+        }
+    for (int W = 1; W < kCtaShapes && rc >= 0 && best < 1e30f; ++W) {
+        float ms = 0.f;
+        if ((rc = time_one(bn, bS, bT, W, &ms)) < 0) break;
+        if (rc == 0 && ms < best) {
+            best = ms;
+            bW = W;
         }
     }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
+    if (rc < 0) return JFOF_ECUDA;
+    if (!(best < 1e30f)) return JFOF_ENOMEM;
+    *best_n_axis = bn;
+    *best_small = bS;
+    *best_dense = bT;
+    *best_shape = bW;
     if (best_ms) *best_ms = best;
-    return best < 1e30f ? JFOF_OK : JFOF_ENOMEM;
+    ctx->tune->best[key] = TuneChoice{double(bn) / double(n0), bS, bT, bW, best};
+    return JFOF_OK;
 }
 
 }  // extern "C"

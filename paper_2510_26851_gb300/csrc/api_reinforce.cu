@@ -84,8 +84,43 @@ int jfof_reinforce_sample(jfof_ctx *ctx, int64_t N, const int32_t *pair_i, const
     if (ws_bytes < sample_layout(N, &counts, ws)) return JFOF_ENOMEM;
     cudaSetDevice(ctx->device);
     CtxScope scope(ctx);
+    // All K samples (chunks of kSampleChunk, four launches each) as one CUDA
+    // graph launched on the context's stream.  It is captured on a
+    // library-owned stream (the caller's may be the legacy default stream,
+    // which cannot be captured); a later call with the same shape updates the
+    // instantiated graph's parameters (seed, pointers) in place.
+    if (!ctx->cap_stream && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return JFOF_ECUDA;
+    Tracer *tr = t_tracer;
+    t_tracer = nullptr;  // no per-launch trace events inside the capture
+    if (cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        t_tracer = tr;
+        return JFOF_ECUDA;
+    }
     launch_reinforce_sample(N, pair_i, pair_j, pair_p, E, K, seed, min_size, counts, labels, n_halos, ctx->dev(),
-                            ctx->stream);
+                            ctx->cap_stream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    t_tracer = tr;
+    if (ce != cudaSuccess) return JFOF_ECUDA;
+    if (ctx->sample_exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(ctx->sample_exec, graph, &info) != cudaSuccess) {
+            cudaGetLastError();  // a different shape: instantiate anew
+            cudaGraphExecDestroy(ctx->sample_exec);
+            ctx->sample_exec = nullptr;
+        }
+    }
+    if (!ctx->sample_exec && cudaGraphInstantiate(&ctx->sample_exec, graph, 0) != cudaSuccess) {
+        ctx->sample_exec = nullptr;
+        cudaGraphDestroy(graph);
+        return JFOF_ECUDA;
+    }
+    cudaGraphDestroy(graph);
+    {
+        JFOF_TRACE("reinforce_sample", ctx->stream);
+        if (cudaGraphLaunch(ctx->sample_exec, ctx->stream) != cudaSuccess) return JFOF_ECUDA;
+    }
     return status_of_launch();
 }
 

@@ -251,7 +251,7 @@ int jfof_fof_stream(jfof_ctx *ctx, const float *h_pos, int64_t N, float L, float
             return JFOF_ECUDA;
         FofBuffers fb;
         fof_layout(Ns, n, &fb, d_ws);
-        LinkParams lp = make_link_params(Ns, L, b, n, ctx->small_threshold, ctx->dense_threshold);
+        LinkParams lp = make_link_params(Ns, L, b, n, ctx->small_threshold, ctx->dense_threshold, ctx->cta_shape);
         launch_bin_cells(d_pos, Ns, L, n, false, lp, fb, ctx->dev(), ctx->stream);
         jfof_cells c{};
         c.n = Ns;

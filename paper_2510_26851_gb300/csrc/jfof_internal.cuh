@@ -269,7 +269,13 @@ inline int64_t cell_table_entries(int n) {
 }  // namespace jfof
 
 // Context (opaque in the C ABI).
-namespace jfof { struct Tracer; struct BatchCache; void destroy_batch_cache(BatchCache *); }
+namespace jfof {
+struct Tracer;
+struct BatchCache;
+void destroy_batch_cache(BatchCache *);
+struct TuneCache;
+void destroy_tune_cache(TuneCache *);
+}  // namespace jfof
 struct jfof_ctx {
     jfof::Tracer *tracer; // null unless tracing is on
     jfof::BatchCache *batch; // cached graph of the last batched call
@@ -280,8 +286,12 @@ struct jfof_ctx {
     int64_t loop_budget;
     int dense_threshold;
     int small_threshold;
+    int cta_shape;           // CTA shape of the list-driven link kernels (tuning knob)
+    jfof::TuneCache *tune;   // autotuner choices per size bucket (first use)
     cudaStream_t copy_stream;  // velocity uploads of jfof_fof_host (created on first use)
     cudaEvent_t ev_pos, ev_vel;
+    cudaStream_t cap_stream;        // capture stream of the REINFORCE sample graph (first use)
+    cudaGraphExec_t sample_exec;    // that graph, updated in place between calls
     jfof::DevStatus dev() const { return jfof::DevStatus{d_status, loop_budget}; }
 };
 

@@ -487,17 +487,18 @@ __device__ __forceinline__ void lunite(int *lp, int a, int b) {
 // cannot take the dense path) links its own pairs through the global forest
 // instead.  Runs before any kernel that unites across cells, since it writes
 // parent with plain stores.
-constexpr int kMedWarps = 4;
+constexpr int kMedWarps = 4;  // default warps per CTA (the autotuner may pick 8)
 constexpr int kMedCap = 256;
 
-__global__ void __launch_bounds__(32 * kMedWarps) medium_local_kernel(const float4 *__restrict__ spos,
+template <int W>
+__global__ void __launch_bounds__(32 * W) medium_local_kernel(const float4 *__restrict__ spos,
                                                                       const uint32_t *__restrict__ cell_start,
                                                                       const uint32_t *__restrict__ medium_cells,
                                                                       const uint32_t *__restrict__ nmedium,
                                                                       uint32_t *next, int64_t M_cap, LinkGeom g,
                                                                       int *parent, DevStatus st) {
-    __shared__ float4 sh_p[kMedWarps][kMedCap];
-    __shared__ int sh_l[kMedWarps][kMedCap];
+    __shared__ float4 sh_p[W][kMedCap];
+    __shared__ int sh_l[W][kMedCap];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     float4 *sp = sh_p[w];
     int *lp = sh_l[w];
@@ -713,7 +714,7 @@ struct SubBox {
 // stores the merged representative on both sides (a stale value only costs
 // an exact union).  A cell of more than 96 particles (possible only when it
 // cannot take the dense path) walks its neighbours one at a time instead.
-constexpr int kMedXWarps = 8;
+constexpr int kMedXWarps = 8;  // default warps per CTA (the autotuner may pick 4)
 constexpr int kMedList = 64;
 constexpr int kMedA = 96;        // cells up to this size take the list path
 constexpr int kMedTaskCap = 256;
@@ -730,7 +731,8 @@ __device__ __forceinline__ uint32_t reach_mask(float4 p, int cx, int cy, int cz,
     return m;
 }
 
-__global__ void __launch_bounds__(32 * kMedXWarps) medium_kernel(const float4 *__restrict__ spos,
+template <int W>
+__global__ void __launch_bounds__(32 * W) medium_kernel(const float4 *__restrict__ spos,
                                                                  const uint32_t *__restrict__ cell_start,
                                                                  const uint32_t *__restrict__ medium_cells,
                                                                  const uint32_t *__restrict__ nmedium,
@@ -738,14 +740,14 @@ __global__ void __launch_bounds__(32 * kMedXWarps) medium_kernel(const float4 *_
                                                                  const uint32_t *__restrict__ dense_id,
                                                                  int64_t M_cap, LinkGeom g, int *parent,
                                                                  DevStatus st) {
-    __shared__ float4 sh_q[kMedXWarps][kMedList];
-    __shared__ int sh_slot[kMedXWarps][kMedList];
-    __shared__ int sh_rep[kMedXWarps][kMedList];
-    __shared__ int sh_pre[kMedXWarps][32];
-    __shared__ float4 sh_pa[kMedXWarps][kMedA];
-    __shared__ int sh_repa[kMedXWarps][kMedA];
-    __shared__ uint32_t sh_amask[kMedXWarps][26][3];
-    __shared__ uint32_t sh_task[kMedXWarps][kMedTaskCap];
+    __shared__ float4 sh_q[W][kMedList];
+    __shared__ int sh_slot[W][kMedList];
+    __shared__ int sh_rep[W][kMedList];
+    __shared__ int sh_pre[W][32];
+    __shared__ float4 sh_pa[W][kMedA];
+    __shared__ int sh_repa[W][kMedA];
+    __shared__ uint32_t sh_amask[W][26][3];
+    __shared__ uint32_t sh_task[W][kMedTaskCap];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     float4 *lq = sh_q[w];
     int *lslot = sh_slot[w], *lrep = sh_rep[w], *pre = sh_pre[w];
@@ -947,7 +949,7 @@ __global__ void __launch_bounds__(32 * kMedXWarps) medium_kernel(const float4 *_
 // the sub-cells outside the largest component, each round over the
 // (sub-cell, non-empty neighbour) tasks spread over the lanes; finally
 // parent[slot] = first slot of the slot's local component.
-constexpr int kDenseWarps = 4;
+constexpr int kDenseWarps = 4;  // default warps per CTA (the autotuner may pick 8)
 
 __device__ __forceinline__ int sub_key(float4 q, const LinkGeom &g, int cx, int cy, int cz) {
     return sub_coord(q.x, g.inv_fine, cx, g.k) +
@@ -1056,7 +1058,8 @@ __device__ void dense_round(const uint32_t *src, int nsrc, int k, const uint16_t
     }
 }
 
-__global__ void __launch_bounds__(32 * kDenseWarps) dense_cells_kernel(float4 *__restrict__ spos,
+template <int W>
+__global__ void __launch_bounds__(32 * W) dense_cells_kernel(float4 *__restrict__ spos,
                                                                        float4 *__restrict__ stage,
                                                                        const uint32_t *__restrict__ cell_start,
                                                                        const uint32_t *__restrict__ dense_cells,
@@ -1064,11 +1067,11 @@ __global__ void __launch_bounds__(32 * kDenseWarps) dense_cells_kernel(float4 *_
                                                                        uint32_t *next, uint16_t *__restrict__ sub_start,
                                                                        uint16_t *__restrict__ sub_rows,
                                                                        int *__restrict__ parent, LinkGeom g) {
-    __shared__ int sh_cnt[kDenseWarps][kSubMax + 1];
-    __shared__ uint16_t sh_ss[kDenseWarps][kSubMax + 2];
-    __shared__ uint32_t sh_ne[kDenseWarps][kSubMax + 1];
-    __shared__ int sh_sz[kDenseWarps][kSubMax + 1];
-    __shared__ uint32_t sh_rows[kDenseWarps][kSubSide * kSubSide];
+    __shared__ int sh_cnt[W][kSubMax + 1];
+    __shared__ uint16_t sh_ss[W][kSubMax + 2];
+    __shared__ uint32_t sh_ne[W][kSubMax + 1];
+    __shared__ int sh_sz[W][kSubMax + 1];
+    __shared__ uint32_t sh_rows[W][kSubSide * kSubSide];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int *cnt = sh_cnt[w];
     uint16_t *ss = sh_ss[w];
@@ -1238,11 +1241,12 @@ __device__ __forceinline__ bool near_box(int cx, int cy, int cz, int k, SubBox &
 // The (source, sub-cell) tasks come from the occupancy rows of the two cells
 // and are spread over the lanes; a task is skipped when its two ends are
 // already in one component, else tested until the first link.
-constexpr int kNbrWarps = 8;
+constexpr int kNbrWarps = 8;  // default warps per CTA (the autotuner may pick 4)
 constexpr int kNbrTaskCap = 512;
 constexpr int kNbrSrcCap = 2 * kSubSide * kSubSide;
 
-__global__ void __launch_bounds__(32 * kNbrWarps) dense_nbr_kernel(const float4 *__restrict__ spos,
+template <int W>
+__global__ void __launch_bounds__(32 * W) dense_nbr_kernel(const float4 *__restrict__ spos,
                                                                    const uint32_t *__restrict__ cell_start,
                                                                    const uint32_t *__restrict__ dense_cells,
                                                                    const uint32_t *__restrict__ ndense, uint32_t *next,
@@ -1250,9 +1254,9 @@ __global__ void __launch_bounds__(32 * kNbrWarps) dense_nbr_kernel(const float4 
                                                                    const uint16_t *__restrict__ sub_start,
                                                                    const uint16_t *__restrict__ sub_rows, LinkGeom g,
                                                                    int *parent, DevStatus st) {
-    __shared__ uint32_t sh_task[kNbrWarps][kNbrTaskCap];
-    __shared__ uint32_t sh_src[kNbrWarps][kNbrSrcCap];
-    __shared__ float4 sh_q[kNbrWarps][32];
+    __shared__ uint32_t sh_task[W][kNbrTaskCap];
+    __shared__ uint32_t sh_src[W][kNbrSrcCap];
+    __shared__ float4 sh_q[W][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint32_t *tasks = sh_task[w];
     uint32_t *srcl = sh_src[w];
@@ -1393,8 +1397,11 @@ __global__ void __launch_bounds__(32 * kNbrWarps) dense_nbr_kernel(const float4 
 }
 
 // ---------------------------------------------------------------------------
-LinkParams make_link_params(int64_t N, float L, float b, int n, int S, int T) {
+LinkParams make_link_params(int64_t N, float L, float b, int n, int S, int T, int shape) {
     LinkParams lp{};
+    const int w[3][4] = {{kMedWarps, kMedXWarps, kDenseWarps, kNbrWarps}, {8, 8, 8, 8}, {4, 4, 4, 4}};
+    const int sh = shape >= 0 && shape < kCtaShapes ? shape : 0;
+    for (int q = 0; q < 4; ++q) lp.warps[q] = w[sh][q];
     double s = double(L) / n;
     int k = int(std::ceil(s * std::sqrt(3.0) * 1.02 / double(b)));
     if (k < 1) k = 1;
@@ -1436,13 +1443,15 @@ void launch_link_core(const jfof_cells &c, const FofBuffers &fb, const LinkParam
     // local passes first: they write parent with plain stores, each for its own cell
     if (lp.T > 0) {
         JFOF_TRACE("dense_cells", s);
-        dense_cells_kernel<<<grid_for(dense_thr, 32 * kDenseWarps, 8), 32 * kDenseWarps, 0, s>>>(
+        auto k = lp.warps[2] == 8 ? dense_cells_kernel<8> : dense_cells_kernel<4>;
+        k<<<grid_for(dense_thr, 32 * lp.warps[2], 8), 32 * lp.warps[2], 0, s>>>(
             fb.spos, fb.tmp, c.cell_start, fb.dense_cells, fb.counters, fb.counters + 2, fb.sub_start, fb.sub_rows,
             fb.parent, g);
     }
     {
         JFOF_TRACE("link_medium_local", s);
-        medium_local_kernel<<<grid_for(med_thr, 32 * kMedWarps, 8), 32 * kMedWarps, 0, s>>>(
+        auto k = lp.warps[0] == 8 ? medium_local_kernel<8> : medium_local_kernel<4>;
+        k<<<grid_for(med_thr, 32 * lp.warps[0], 8), 32 * lp.warps[0], 0, s>>>(
             spos, c.cell_start, fb.medium_cells, fb.counters + 1, fb.counters + 3, medium_cap(N), g, fb.parent, st);
     }
     // then everything that unites across cells (atomic hooks only)
@@ -1453,13 +1462,15 @@ void launch_link_core(const jfof_cells &c, const FofBuffers &fb, const LinkParam
     }
     {
         JFOF_TRACE("link_medium", s);
-        medium_kernel<<<grid_for(med_thr, 32 * kMedXWarps, 8), 32 * kMedXWarps, 0, s>>>(
+        auto k = lp.warps[1] == 4 ? medium_kernel<4> : medium_kernel<8>;
+        k<<<grid_for(med_thr, 32 * lp.warps[1], 8), 32 * lp.warps[1], 0, s>>>(
             spos, c.cell_start, fb.medium_cells, fb.counters + 1, fb.counters + 4, fb.dense_id, medium_cap(N), g,
             fb.parent, st);
     }
     if (lp.T > 0) {
         JFOF_TRACE("link_dense_nbr", s);
-        dense_nbr_kernel<<<grid_for(dense_thr, 32 * kNbrWarps, 8), 32 * kNbrWarps, 0, s>>>(
+        auto k = lp.warps[3] == 4 ? dense_nbr_kernel<4> : dense_nbr_kernel<8>;
+        k<<<grid_for(dense_thr, 32 * lp.warps[3], 8), 32 * lp.warps[3], 0, s>>>(
             spos, c.cell_start, fb.dense_cells, fb.counters, fb.counters + 5, fb.dense_id, fb.sub_start, fb.sub_rows,
             g, fb.parent, st);
     }

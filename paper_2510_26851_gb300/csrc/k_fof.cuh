@@ -54,13 +54,18 @@ struct FofBuffers {
     uint32_t *bin_base;    // [bricks * kFewGrid + 1] their brick-major exclusive scan
 };
 
-// Dense-path parameters derived on the host from (N, L, b, n, T).
+// Dense-path parameters derived on the host from (N, L, b, n, T), and the
+// CTA shape of the list-driven link kernels (a tuning knob; results do not
+// depend on it): warps per CTA of medium_local, medium, dense_cells and
+// dense_nbr.  Shape 0 = (4, 8, 4, 8), 1 = all 8, 2 = all 4.
+constexpr int kCtaShapes = 3;
 struct LinkParams {
     int S;          // small cells: at most S particles
     int T;          // dense threshold actually used (0 = dense path off)
     int k;          // sub-cells per cell side
     float inv_fine; // f32(n k / L)
     int64_t D_cap;  // dense cells with a sub-cell table
+    int warps[4];   // warps per CTA of the four list-driven link kernels
 };
 
 size_t fof_layout(int64_t N, int n, FofBuffers *fb, void *base);
@@ -70,7 +75,7 @@ bool finite_pos(float x);
 int check_box(int64_t N, float L, float b);
 int32_t max_cells(float L, float b);
 int resolve_n(int64_t N, float L, float b, int32_t n_axis, int32_t *out);
-LinkParams make_link_params(int64_t N, float L, float b, int n, int S, int T);
+LinkParams make_link_params(int64_t N, float L, float b, int n, int S, int T, int shape = 0);
 void launch_bin_cells(const float *pos, int64_t N, float L, int n, bool wrap, const LinkParams &lp,
                       const FofBuffers &fb, const DevStatus &st, cudaStream_t s);
 // Union-find over the cell grid (parent[] complete, not yet flattened).

@@ -90,13 +90,55 @@ def test_autotuner_choice_keeps_labels(J):
     spec = synth.BoxSpec("t", 400_000, 73.0, synth.linking_length(73.0, 400_000), 2400, 0.6, 12,
                          velocities=False)
     pos, _ = synth.generate(spec, device="cuda", velocities=False)
-    n, S, T, ms = J.autotune(pos, spec.L, spec.b, spec.min_size)
-    assert ms > 0 and n >= 3
+    n, S, T, W, ms = J.autotune(pos, spec.L, spec.b, spec.min_size)
+    assert ms > 0 and n >= 3 and W in (0, 1, 2)
+    # the same size bucket: the kept choice comes back without timing
+    assert J.autotune(pos, spec.L, spec.b, spec.min_size, use_cache=True) == (n, S, T, W, ms)
     ref = oracle.fof_labels(pos.cpu().numpy(), spec.L, spec.b)
     try:
         J.set_cell_classes(S, T)
+        J.set_cta_shape(W)
         r = J.fof(pos, spec.L, spec.b, spec.min_size, n_axis=n)
         J.sync()
     finally:
         J.set_cell_classes()
+        J.set_cta_shape(0)
     assert np.array_equal(r.label.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("shape", [0, 1, 2])
+def test_labels_do_not_depend_on_the_cta_shape(J, shape):
+    # every CTA shape of the four list-driven link kernels, with many dense
+    # and medium cells (a low dense threshold)
+    spec = synth.BoxSpec("t", 300_000, 50.0, synth.linking_length(50.0, 300_000), 2500, 0.7, 14,
+                         velocities=False)
+    pos, _ = synth.generate(spec, device="cuda", velocities=False)
+    ref = oracle.fof_labels(pos.cpu().numpy(), spec.L, spec.b)
+    try:
+        J.set_cta_shape(shape)
+        for S, T in ((8, 96), (4, 32)):
+            J.set_cell_classes(S, T)
+            r = J.fof(pos, spec.L, spec.b, spec.min_size)
+            J.sync()
+            assert np.array_equal(r.label.cpu().numpy(), ref), (shape, S, T)
+    finally:
+        J.set_cell_classes()
+        J.set_cta_shape(0)
+
+
+def test_tuned_batch_matches_oracle(J):
+    rng = np.random.default_rng(5)
+    specs = []
+    for k, N in enumerate([40_000, 90_000, 40_000, 250_000, 7_000, 90_000]):
+        L = float(np.float32(rng.uniform(40, 90)))
+        specs.append(synth.BoxSpec(f"u{k}", N, L, synth.linking_length(L, N), max(1, N // 200), 0.6, 40 + k,
+                                   velocities=False))
+    pos, off = make_batch(specs)
+    bt, picks = J.Batch.tuned(pos, off, [s.L for s in specs], [s.b for s in specs], min_size=20, reps=1)
+    assert len(picks) == len(specs)
+    lab, hid, nh = [t.cpu().numpy().copy() for t in bt.run(pos, use_graph=True)]
+    J.sync()
+    pos_np = pos.cpu().numpy()
+    for k, sp in enumerate(specs):
+        s, e = off[k], off[k + 1]
+        check_box(J, pos_np[s:e], sp, lab[s:e], hid[s:e], nh[k])
