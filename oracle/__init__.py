@@ -215,6 +215,26 @@ def halo_props_backward(vel, halo_id, H: int, vmean, sigv, g_com=None, g_vmean=N
     return gp, gv
 
 
+def subhalo_labels(pos, vel, halo_id, H: int, L: float, sigma_x: float, sigma_v: float) -> np.ndarray:
+    """Phase-space sub-halo labels (Eq. 3): smallest index of each particle's
+    6-D group inside its halo; particles outside halos are their own group.
+    1/sigma are rounded once to binary32 (infinite sigma switches a term off)."""
+    c = ctypes
+    lib = _load()
+    lib.orc_subhalo_labels.restype = c.c_int
+    lib.orc_subhalo_labels.argtypes = [_f32p, _f32p, _i32p, c.c_int64, c.c_int64, c.c_float, c.c_float,
+                                       c.c_float, _i32p]
+    p = _pos32(pos)
+    v = _pos32(vel)
+    out = np.empty(p.shape[0], np.int32)
+    inv = lambda s: np.float32(0.0) if np.isinf(s) else np.float32(1.0 / float(s))  # noqa: E731
+    st = lib.orc_subhalo_labels(p, v, np.ascontiguousarray(halo_id, np.int32), p.shape[0], H, np.float32(L),
+                                inv(sigma_x), inv(sigma_v), out)
+    if st != 0:
+        raise OracleError(f"orc_subhalo_labels status {st}")
+    return out
+
+
 def _declare_decor(lib):
     c = ctypes
     lib.orc_halo_decoration.restype = c.c_int

@@ -755,6 +755,84 @@ int orc_halo_props_backward(const double *vel, const int32_t *halo_id, int64_t N
 }
 
 /* ------------------------------------------------------------------------ */
+/* Sub-halos: a second FoF pass inside each halo in phase space (Sec. 2.1.1, */
+/* Eq. 3): members i, j of one halo are friends when                         */
+/*   |x_i - x_j|^2 / sigma_x + |v_i - v_j|^2 / sigma_v <= 1,                 */
+/* with the minimum-image position difference.  Binary32, in this order and  */
+/* with no fused operations (both sides evaluate it the same way):           */
+/*   dxx = (dx*dx + dy*dy) + dz*dz,  dvv = (du*du + dv*dv) + dw*dw,          */
+/*   link iff dxx * inv_sx + dvv * inv_sv <= 1,                               */
+/* inv_sx = f32(1/sigma_x), inv_sv = f32(1/sigma_v) (0 switches a term off).  */
+/* sub_label[i] = smallest index of i's phase-space group inside its halo;   */
+/* a particle outside every halo (halo_id = -1) is its own group.            */
+
+float orc_phase_d2(const float *pi, const float *pj, const float *vi, const float *vj, float L,
+                   float inv_sx, float inv_sv)
+{
+    float hL = 0.5f * L;
+    float dx = orc_min_image(pj[0], pi[0], L, hL);
+    float dy = orc_min_image(pj[1], pi[1], L, hL);
+    float dz = orc_min_image(pj[2], pi[2], L, hL);
+    float du = vj[0] - vi[0];
+    float dv = vj[1] - vi[1];
+    float dw = vj[2] - vi[2];
+    float sxx = dx * dx;
+    float syy = dy * dy;
+    float szz = dz * dz;
+    float dxx = sxx + syy;
+    dxx = dxx + szz;
+    float suu = du * du;
+    float svv = dv * dv;
+    float sww = dw * dw;
+    float dvv = suu + svv;
+    dvv = dvv + sww;
+    float a = dxx * inv_sx;
+    float c = dvv * inv_sv;
+    return a + c;
+}
+
+int orc_subhalo_labels(const float *pos, const float *vel, const int32_t *halo_id, int64_t N,
+                       int64_t H, float L, float inv_sx, float inv_sv, int32_t *sub_label)
+{
+    int64_t *start = (int64_t *)calloc((size_t)H + 1, sizeof(int64_t));
+    int32_t *mem = (int32_t *)malloc(sizeof(int32_t) * (size_t)(N > 0 ? N : 1));
+    if (!start || !mem) {
+        free(start); free(mem);
+        return ORC_ENOMEM;
+    }
+    /* members of each halo in ascending index */
+    for (int64_t i = 0; i < N; ++i)
+        if (halo_id[i] >= 0)
+            start[halo_id[i] + 1] += 1;
+    for (int64_t h = 0; h < H; ++h)
+        start[h + 1] += start[h];
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)(H > 0 ? H : 1));
+    if (!fill) {
+        free(start); free(mem);
+        return ORC_ENOMEM;
+    }
+    memcpy(fill, start, sizeof(int64_t) * (size_t)H);
+    for (int64_t i = 0; i < N; ++i)
+        if (halo_id[i] >= 0)
+            mem[fill[halo_id[i]]++] = (int32_t)i;
+    free(fill);
+    for (int64_t i = 0; i < N; ++i)
+        sub_label[i] = (int32_t)i;
+    /* every pair of members of one halo, once; the smaller index is the root */
+    for (int64_t h = 0; h < H; ++h)
+        for (int64_t a = start[h]; a < start[h + 1]; ++a)
+            for (int64_t c = a + 1; c < start[h + 1]; ++c) {
+                int32_t i = mem[a], j = mem[c];
+                if (orc_phase_d2(pos + 3 * i, pos + 3 * j, vel + 3 * i, vel + 3 * j, L, inv_sx, inv_sv) <= 1.0f)
+                    uf_union(sub_label, i, j);
+            }
+    for (int64_t i = 0; i < N; ++i)
+        sub_label[i] = uf_find(sub_label, (int32_t)i);
+    free(start); free(mem);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Decorated frozen assignment (Sec. 3.1.1, Eq. 5): a halo "decoration" that  */
 /* is an analytic function of the member positions, here the particle        */
 /* standard deviation about the halo centre,                                 */

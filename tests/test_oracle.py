@@ -729,3 +729,88 @@ def test_decorated_mass_function_gradient_chain():
             fd = (loss(p1) - loss(p0)) / (2 * eps)
             assert abs(g[i, a] - fd) < 1e-6 * max(1.0, abs(fd)), (i, a)
     assert np.abs(g).max() > 1e-3
+
+
+# --------------------------------------------------------------------------
+# Sub-halos: FoF in phase space inside each halo (Sec. 2.1.1, Eq. 3)
+
+def _halos_of(pos, L, b, min_size):
+    lab = oracle.fof_labels(pos, L, b)
+    hid, cnt = oracle.groups(lab, min_size)
+    return hid, len(cnt)
+
+
+def _subhalo_reference_by_position(pos, hid, H, L, b):
+    # per halo: brute-force FoF of its members alone, local labels -> indices
+    out = np.arange(pos.shape[0], dtype=np.int32)
+    for h in range(H):
+        m = np.nonzero(hid == h)[0]
+        loc = oracle.fof_brute(pos[m], L, b)
+        out[m] = m[loc]
+    return out
+
+
+def test_subhalo_equal_velocities_is_fof_of_each_halo():
+    # identical velocities and sigma_x = 1/4 (1/sigma_x = 4 exactly): the
+    # phase-space test is exactly d2 <= (1/2)^2, so each halo splits as the
+    # brute-force FoF of its members with b = 1/2
+    spec = synth.BoxSpec("t", 4000, 30.0, 1.0, 25, 0.7, 6)
+    pos, _ = synth.generate(spec, velocities=False)
+    pos = pos.numpy()
+    hid, H = _halos_of(pos, spec.L, 1.0, 10)
+    assert H > 5
+    vel = np.tile(np.float32([3.0, -2.0, 5.0]), (pos.shape[0], 1))
+    got = oracle.subhalo_labels(pos, vel, hid, H, spec.L, 0.25, 1.0)
+    want = _subhalo_reference_by_position(pos, hid, H, spec.L, 0.5)
+    assert np.array_equal(got, want)
+    assert len(set(got[hid >= 0].tolist())) > H  # the halos do split
+    # an infinite velocity scale switches the velocity term off
+    vel2 = np.random.default_rng(1).normal(0, 100, pos.shape).astype(np.float32)
+    assert np.array_equal(oracle.subhalo_labels(pos, vel2, hid, H, spec.L, 0.25, np.inf), want)
+
+
+def test_subhalo_splits_coincident_streams():
+    # two interpenetrating clumps, one halo in position, two in phase space
+    rng = np.random.default_rng(7)
+    L = 20.0
+    a = 10.0 + rng.normal(0, 0.05, (300, 3))
+    b = 10.0 + rng.normal(0, 0.05, (300, 3))
+    pos = np.concatenate([a, b]).astype(np.float32)
+    vel = np.concatenate([np.tile([200.0, 0, 0], (300, 1)) + rng.normal(0, 1, (300, 3)),
+                          np.tile([-200.0, 0, 0], (300, 1)) + rng.normal(0, 1, (300, 3))]).astype(np.float32)
+    perm = rng.permutation(600)
+    pos, vel = pos[perm], vel[perm]
+    hid, H = _halos_of(pos, L, 0.1, 20)
+    assert H == 1 and (hid == 0).all()
+    sub = oracle.subhalo_labels(pos, vel, hid, H, L, 0.2 ** 2, 20.0 ** 2)
+    stream = (vel[:, 0] > 0)
+    assert len(set(sub[stream].tolist())) == 1 and len(set(sub[~stream].tolist())) == 1
+    assert sub[stream][0] != sub[~stream][0]
+    assert sub[stream][0] == np.nonzero(stream)[0].min()
+
+
+def test_subhalo_invariants_on_a_clustered_box():
+    spec = synth.BoxSpec("t", 6000, 25.0, synth.linking_length(25.0, 6000) * 1.3, 40, 0.7, 9)
+    pos, vel = synth.generate(spec)
+    pos, vel = pos.numpy(), vel.numpy()
+    hid, H = _halos_of(pos, spec.L, spec.b, 20)
+    sx, sv = (0.5 * spec.b) ** 2, 40.0 ** 2
+    sub = oracle.subhalo_labels(pos, vel, hid, H, spec.L, sx, sv)
+    inv_sx, inv_sv = np.float32(1 / sx), np.float32(1 / sv)
+
+    def d2(i, j):
+        return oracle.dist2(pos[i], pos[j], spec.L) * inv_sx + float(np.sum((vel[j] - vel[i]) ** 2)) * inv_sv
+
+    N = pos.shape[0]
+    assert np.all(sub[hid < 0] == np.nonzero(hid < 0)[0])
+    for h in range(H):
+        m = np.nonzero(hid == h)[0]
+        assert np.all(hid[sub[m]] == h) and np.all(sub[m] <= m)  # inside the halo, smallest member
+        for g in np.unique(sub[m]):
+            grp = m[sub[m] == g]
+            assert g == grp.min()
+            rest = m[sub[m] != g]
+            for i in grp[:20]:
+                # no member outside the group is a phase-space friend (with a margin)
+                assert all(d2(i, j) > 1.0 + 1e-5 for j in rest[:200])
+    assert len(np.unique(sub[hid >= 0])) > H
