@@ -49,19 +49,69 @@ __device__ __forceinline__ float load_coord(const float *pos, int64_t i, int a, 
     return wrap ? wrap_coord(x, L) : x;
 }
 
-// One warp per halo (grid-stride over halos).  Pass 1 gathers the members:
-// positions are summed as minimum-image offsets from the halo's first member
-// xr (periodic centre of mass) and velocities as offsets from that member's
-// velocity vr, giving vmean = vr + S1/m.  Pass 2 sums |v - vmean|^2 about
-// that mean (the dispersion of the design notes, two-pass): no cancellation
-// between large terms, whatever vr is (a cold halo whose first member is a
-// velocity outlier included).  The first 64 members' velocities stay in
-// registers between the passes; larger halos gather them again (L2 hits).
-__device__ __forceinline__ void load_vel(const float *__restrict__ vel, int64_t i, float v[3]) {
+// Running (count, mean, sum of squared deviations) of a lane's velocities
+// (Welford's update) and the exact pairwise merge of two such summaries
+// (Chan, Golub & LeVeque): M2 = M2a + M2b + d^2 na nb / (na + nb) with
+// d = mean_b - mean_a.  Every term added to M2 is non-negative, so no large
+// terms cancel whatever the velocities are (a cold halo whose first member is
+// an outlier included); the mean is a compensated-free running average whose
+// rounding enters M2 only at second order.
+struct Moments {
+    float n, m[3], M2;
+};
+
+__device__ __forceinline__ void welford(Moments &a, const float v[3]) {
+    a.n = __fadd_rn(a.n, 1.0f);
+    const float r = __frcp_rn(a.n);
+    float q = 0.f;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) v[a] = vel[3 * i + a];
+    for (int c = 0; c < 3; ++c) {
+        const float d = __fsub_rn(v[c], a.m[c]);
+        a.m[c] = __fadd_rn(a.m[c], __fmul_rn(d, r));
+        q = __fadd_rn(q, __fmul_rn(d, __fsub_rn(v[c], a.m[c])));
+    }
+    a.M2 = __fadd_rn(a.M2, q);
 }
 
+__device__ __forceinline__ Moments chan(const Moments &a, const Moments &b) {
+    if (a.n == 0.f) return b;
+    if (b.n == 0.f) return a;
+    Moments r;
+    r.n = __fadd_rn(a.n, b.n);
+    const float wb = __fdiv_rn(b.n, r.n);
+    float dd = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float d = __fsub_rn(b.m[c], a.m[c]);
+        r.m[c] = __fadd_rn(a.m[c], __fmul_rn(d, wb));
+        dd = __fadd_rn(dd, __fmul_rn(d, d));
+    }
+    r.M2 = __fadd_rn(__fadd_rn(a.M2, b.M2), __fmul_rn(dd, __fmul_rn(a.n, wb)));
+    return r;
+}
+
+// Warp merge in a fixed butterfly order (each pair merges lower lane first,
+// so all lanes end with the same summary).
+__device__ __forceinline__ Moments chan_warp(Moments a) {
+    const int lane = threadIdx.x & 31;
+    for (int o = 16; o > 0; o >>= 1) {
+        Moments b;
+        b.n = __shfl_xor_sync(0xffffffffu, a.n, o);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) b.m[c] = __shfl_xor_sync(0xffffffffu, a.m[c], o);
+        b.M2 = __shfl_xor_sync(0xffffffffu, a.M2, o);
+        a = (lane & o) ? chan(b, a) : chan(a, b);
+    }
+    return a;
+}
+
+// One warp per halo (grid-stride over halos), one gather pass over the
+// members.  Positions are summed as minimum-image offsets from the halo's
+// first member xr (periodic centre of mass) and velocities as offsets from
+// that member's velocity vr, both compensated: vmean = vr + S1/m.  The
+// dispersion comes from the Welford summaries of each lane's velocities,
+// merged across the warp by Chan's formula: sigma^2 = M2 / (3 m), with no
+// cancellation.
 __global__ void __launch_bounds__(256) halo_props_kernel(const float *__restrict__ pos, const float *__restrict__ vel,
                                                          float L, bool wrap, const int32_t *__restrict__ halo_start,
                                                          const int32_t *__restrict__ members,
@@ -86,7 +136,7 @@ __global__ void __launch_bounds__(256) halo_props_kernel(const float *__restrict
         }
         KSum sx[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         KSum sv[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-        float c0[3] = {0.f, 0.f, 0.f}, c1[3] = {0.f, 0.f, 0.f};  // members hs+lane, hs+lane+32
+        Moments mv{0.f, {0.f, 0.f, 0.f}, 0.f};
         for (int k0 = hs + lane; k0 < he; k0 += 64) {
             // two members per lane per step: all six gathers issue before the sums
             int k1 = k0 + 32;
@@ -98,28 +148,24 @@ __global__ void __launch_bounds__(256) halo_props_kernel(const float *__restrict
             for (int a = 0; a < 3; ++a) {
                 p0[a] = load_coord(pos, i0, a, L, wrap);
                 p1[a] = load_coord(pos, i1, a, L, wrap);
-            }
-            if (vel) {
-                load_vel(vel, i0, v0);
-                load_vel(vel, i1, v1);
-            }
-            if (k0 == hs + lane) {
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    c0[a] = v0[a];
-                    c1[a] = v1[a];
+                if (vel) {
+                    v0[a] = vel[3 * int64_t(i0) + a];
+                    v1[a] = vel[3 * int64_t(i1) + a];
                 }
             }
 #pragma unroll
-            for (int t = 0; t < 2; ++t) {
-                if (t == 1 && !two) break;
-                const float *p = t ? p1 : p0;
-                const float *v = t ? v1 : v0;
+            for (int a = 0; a < 3; ++a) {
+                kadd(sx[a], min_image(p0[a], xr[a], L, hL));
+                if (vel) kadd(sv[a], __fsub_rn(v0[a], vr[a]));
+            }
+            if (vel) welford(mv, v0);
+            if (two) {
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    kadd(sx[a], min_image(p[a], xr[a], L, hL));
-                    if (vel) kadd(sv[a], __fsub_rn(v[a], vr[a]));
+                    kadd(sx[a], min_image(p1[a], xr[a], L, hL));
+                    if (vel) kadd(sv[a], __fsub_rn(v1[a], vr[a]));
                 }
+                if (vel) welford(mv, v1);
             }
         }
         float vm[3];
@@ -132,30 +178,11 @@ __global__ void __launch_bounds__(256) halo_props_kernel(const float *__restrict
         }
         if (lane == 0) mass[h] = __fmul_rn(particle_mass, fm);
         if (!vel) continue;
-        // pass 2: squared deviations from the mean
-        KSum s2 = {0.f, 0.f};
-        auto dev2 = [&](const float v[3]) {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                float d = __fsub_rn(v[a], vm[a]);
-                kadd(s2, __fmul_rn(d, d));
-            }
-        };
-        if (m <= 64) {
-            if (lane < m) dev2(c0);
-            if (lane + 32 < m) dev2(c1);
-        } else {
-            for (int k = hs + lane; k < he; k += 32) {
-                float v[3];
-                load_vel(vel, members[k], v);
-                dev2(v);
-            }
-        }
-        float var = __fdiv_rn(kval(kwarp(s2)), __fmul_rn(3.0f, fm));
+        const Moments t = chan_warp(mv);
         if (lane == 0) {
 #pragma unroll
             for (int a = 0; a < 3; ++a) vmean[3 * h + a] = vm[a];
-            sigv[h] = __fsqrt_rn(fmaxf(var, 0.f));
+            sigv[h] = __fsqrt_rn(fmaxf(__fdiv_rn(t.M2, __fmul_rn(3.0f, fm)), 0.f));
         }
     }
 }
