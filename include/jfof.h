@@ -311,13 +311,16 @@ int jfof_fof_batched(jfof_ctx *ctx, const float *pos, const int64_t *h_box_offse
    fastest choice (*best_n_axis, *best_small, *best_dense, *best_shape) and
    its time in ms.  The choice is kept in the context by size bucket
    (round(2 log2 N), round(4 log2(L/b))); use_cache != 0 returns a kept choice
-   for the same bucket without timing.  Synchronises.  Outputs label/halo_id
-   [N] and n_halos [1] are scratch for the trials.  Labels never depend on
-   the choice. */
+   for the same bucket without timing.  flush (device, may be NULL): a buffer
+   larger than L2 that is overwritten before every timed run, so that boxes
+   smaller than L2 are timed with their data in DRAM, as inside a batch.
+   Synchronises.  Outputs label/halo_id [N] and n_halos [1] are scratch for
+   the trials.  Labels never depend on the choice. */
 int jfof_autotune(jfof_ctx *ctx, const float *pos, int64_t N, float L, float b, uint32_t flags,
                   int32_t min_size, void *ws, size_t ws_bytes, int32_t *label, int32_t *halo_id,
-                  int32_t *n_halos, int32_t reps, int32_t use_cache, int32_t *best_n_axis,
-                  int32_t *best_small, int32_t *best_dense, int32_t *best_shape, float *best_ms);
+                  int32_t *n_halos, int32_t reps, int32_t use_cache, void *flush, size_t flush_bytes,
+                  int32_t *best_n_axis, int32_t *best_small, int32_t *best_dense, int32_t *best_shape,
+                  float *best_ms);
 
 /* Convenience: a1-a7 in one call (bin, link, groups) with one workspace. */
 int jfof_fof_all_bytes(int64_t N, int32_t n_axis, size_t *bytes);
@@ -345,6 +348,29 @@ int jfof_fof_host(jfof_ctx *ctx, const float *h_pos, const float *h_vel, int64_t
                   float *d_vel, void *ws, size_t ws_bytes, int32_t *label, int32_t *halo_id,
                   int32_t *count, int32_t *halo_start, int32_t *members, int32_t *n_halos,
                   float *mass, float *com, float *vmean, float *sigv);
+
+/* ---------------------------------------------------------------------- */
+/* Sub-halos (Sec. 2.1.1, Eq. 3): a second FoF pass inside each halo in     */
+/* phase space.  Members i, j of one halo are friends when                  */
+/*   |x_i - x_j|^2 / sigma_x + |v_i - v_j|^2 / sigma_v <= 1                  */
+/* (minimum-image dx), evaluated in binary32 as dxx = (dx*dx + dy*dy) +      */
+/* dz*dz, dvv likewise, link iff dxx*f32(1/sigma_x) + dvv*f32(1/sigma_v) <=   */
+/* 1, each operation rounded once (sigma = +inf switches its term off).      */
+
+/* Workspace bytes for jfof_subhalos (member-ordered positions, velocities  */
+/* and a forest over member slots: 36 B per particle). */
+int jfof_subhalos_bytes(int64_t N, size_t *bytes);
+
+/* sub_label[N] (device int32): for a member of a halo, the smallest index   */
+/* of its phase-space group inside that halo; for a particle outside every   */
+/* halo, its own index.  pos, vel float32 [N,3] (JFOF_WRAP as jfof_fof);     */
+/* halo_start/members/n_halos: the CSR of jfof_groups or jfof_fof.  Feeding  */
+/* sub_label to jfof_groups gives sub-halo ids and sizes.  Each halo's pairs */
+/* are all tested (cost grows with the square of the halo size). */
+int jfof_subhalos(jfof_ctx *ctx, const float *pos, const float *vel, int64_t N, float L,
+                  uint32_t flags, const int32_t *halo_start, const int32_t *members,
+                  const int32_t *n_halos, int64_t H_cap, float sigma_x, float sigma_v, void *ws,
+                  size_t ws_bytes, int32_t *sub_label);
 
 /* ---------------------------------------------------------------------- */
 /* Decorated frozen assignment (Sec. 3.1.1, Eq. 5) and the soft mass        */

@@ -33,7 +33,7 @@ EXPORTED = [
     "jfof_eval_edge_uniform", "jfof_batch_bytes", "jfof_fof_batched", "jfof_autotune",
     "jfof_fof_static", "jfof_fof_host", "jfof_slab_select", "jfof_merge_labels", "jfof_fof_stream_bytes",
     "jfof_fof_stream", "jfof_halo_decoration", "jfof_halo_decoration_backward", "jfof_soft_hmf_bytes",
-    "jfof_soft_hmf", "jfof_soft_hmf_backward",
+    "jfof_soft_hmf", "jfof_soft_hmf_backward", "jfof_subhalos_bytes", "jfof_subhalos",
 ]
 
 
@@ -95,8 +95,8 @@ def _declare(lib):
         "jfof_eval_edge_uniform": [vp, c.c_uint64, vp, vp, vp, vp, i64],
         "jfof_batch_bytes": [vp, i32, vp, vp, vp, i32, P(sz)],
         "jfof_fof_batched": [vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, u32, i32, vp, sz, vp, vp, vp, i32],
-        "jfof_autotune": [vp, vp, i64, f32, f32, u32, i32, vp, sz, vp, vp, vp, i32, i32, P(i32), P(i32),
-                          P(i32), P(i32), P(f32)],
+        "jfof_autotune": [vp, vp, i64, f32, f32, u32, i32, vp, sz, vp, vp, vp, i32, i32, vp, sz, P(i32),
+                          P(i32), P(i32), P(i32), P(f32)],
         "jfof_fof_static": [vp, vp, i64, f32, f32, i32, u32, i32, vp, vp, vp, vp, vp, vp],
         "jfof_fof_host": [vp, vp, vp, i64, f32, f32, i32, u32, i32, f32, vp, vp, vp, sz, vp, vp, vp, vp, vp,
                           vp, vp, vp, vp, vp],
@@ -109,6 +109,8 @@ def _declare(lib):
         "jfof_soft_hmf_bytes": [i64, i32, P(sz)],
         "jfof_soft_hmf": [vp, vp, vp, i64, f32, vp, i32, f32, vp, sz, vp],
         "jfof_soft_hmf_backward": [vp, vp, vp, i64, f32, vp, vp, i32, f32, f32, vp, vp],
+        "jfof_subhalos_bytes": [i64, P(sz)],
+        "jfof_subhalos": [vp, vp, vp, i64, f32, u32, vp, vp, vp, i64, f32, f32, vp, sz, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -656,6 +658,18 @@ def set_cta_shape(shape: int = 0, device=None):
     _check(library().jfof_set_cta_shape(context(device), shape), "jfof_set_cta_shape")
 
 
+_flush = {}
+
+
+def _flush_buffer(dev) -> torch.Tensor:
+    """A 256 MiB device buffer (twice the L2) the autotuner overwrites before
+    each timed run."""
+    key = str(dev)
+    if key not in _flush:
+        _flush[key] = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    return _flush[key]
+
+
 def autotune(pos: torch.Tensor, L: float, b: float, min_size: int = 20, reps: int = 2,
              wrap: bool = False, use_cache: bool = False):
     """Fastest (n_axis, small, dense, cta_shape, ms) for this box among the
@@ -673,10 +687,12 @@ def autotune(pos: torch.Tensor, L: float, b: float, min_size: int = 20, reps: in
     hid = torch.empty(N, dtype=torch.int32, device=dev)
     nh = torch.empty(1, dtype=torch.int32, device=dev)
     bn, bs, bd, bw, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    flush = _flush_buffer(dev)
     _check(library().jfof_autotune(context(dev), _ptr(pos), N, L, b, JFOF_WRAP if wrap else 0, min_size,
                                    _ptr(ws), ws.numel(), _ptr(label), _ptr(hid), _ptr(nh), reps,
-                                   1 if use_cache else 0, ctypes.byref(bn), ctypes.byref(bs), ctypes.byref(bd),
-                                   ctypes.byref(bw), ctypes.byref(ms)), "jfof_autotune")
+                                   1 if use_cache else 0, _ptr(flush), flush.numel(), ctypes.byref(bn),
+                                   ctypes.byref(bs), ctypes.byref(bd), ctypes.byref(bw), ctypes.byref(ms)),
+           "jfof_autotune")
     return bn.value, bs.value, bd.value, bw.value, ms.value
 
 
@@ -909,3 +925,25 @@ class DecoratedHMF(torch.autograd.Function):
         g_dsig = soft_hmf_backward(ctx.g, dsig, edges, ctx.width, ctx.kappa, g_hist.float(), ctx.mp)
         g_pos = halo_decoration_backward(pos, ctx.L, ctx.g, com, dsig, g_dsig, wrap=ctx.wrap)
         return g_pos, None, None, None, None, None, None, None
+
+
+# ---------------------------------------------------------------------------
+# Sub-halos: FoF in phase space inside each halo (Sec. 2.1.1, Eq. 3).
+
+def subhalos(pos: torch.Tensor, vel: torch.Tensor, L: float, g: Groups, sigma_x: float, sigma_v: float,
+             wrap: bool = False) -> torch.Tensor:
+    """sub_label[N]: smallest index of each member's phase-space group inside
+    its halo (|dx|^2/sigma_x + |dv|^2/sigma_v <= 1); non-members keep their
+    own index.  :func:`groups` on the result gives sub-halo ids."""
+    _need(pos, torch.float32, None, "pos")
+    _need(vel, torch.float32, tuple(pos.shape), "vel")
+    N = pos.shape[0]
+    nb = ctypes.c_size_t()
+    _check(library().jfof_subhalos_bytes(N, ctypes.byref(nb)), "jfof_subhalos_bytes")
+    ws = _ws(nb.value, pos.device)
+    out = torch.empty(N, dtype=torch.int32, device=pos.device)
+    _check(library().jfof_subhalos(context(pos.device), _ptr(pos), _ptr(vel), N, L, JFOF_WRAP if wrap else 0,
+                                   _ptr(g.halo_start), _ptr(g.members), _ptr(g.n_halos_dev), g.H_cap,
+                                   float(sigma_x), float(sigma_v), _ptr(ws), ws.numel(), _ptr(out)),
+           "jfof_subhalos")
+    return out

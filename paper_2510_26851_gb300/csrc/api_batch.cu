@@ -266,11 +266,14 @@ int jfof_fof_batched(jfof_ctx *ctx, const float *pos, const int64_t *h_box_offse
 // best of those, and returns the fastest.  The choice is kept in the context
 // by size bucket (round(2 log2 N), round(4 log2(L/b))); with use_cache a box
 // of a known bucket gets it back without timing (*best_ms = the time it was
-// chosen with).  Synchronises.  Labels do not depend on the choice.
+// chosen with).  With a flush buffer (larger than L2), each timed run starts
+// after the buffer is overwritten, so a small box is timed with its data in
+// DRAM as it would be inside a batch, not resident in L2 from the run before.
+// Synchronises.  Labels do not depend on the choice.
 int jfof_autotune(jfof_ctx *ctx, const float *pos, int64_t N, float L, float b, uint32_t flags, int32_t min_size,
                   void *ws, size_t ws_bytes, int32_t *label, int32_t *halo_id, int32_t *n_halos, int32_t reps,
-                  int32_t use_cache, int32_t *best_n_axis, int32_t *best_small, int32_t *best_dense,
-                  int32_t *best_shape, float *best_ms) {
+                  int32_t use_cache, void *flush, size_t flush_bytes, int32_t *best_n_axis, int32_t *best_small,
+                  int32_t *best_dense, int32_t *best_shape, float *best_ms) {
     if (!ctx || !pos || !ws || !label || !halo_id || !n_halos || !best_n_axis || !best_small || !best_dense ||
         !best_shape || reps < 1)
         return JFOF_EINVAL;
@@ -320,13 +323,18 @@ int jfof_autotune(jfof_ctx *ctx, const float *pos, int64_t N, float L, float b, 
         BoxPlan p = plan_box(N, L, b, n, S, T, W, min_size);
         if (p.total > ws_bytes) return 1;
         run_box(p, pos, flags, min_size, reinterpret_cast<char *>(ws), label, halo_id, n_halos, st, ctx->stream);
-        cudaEventRecord(t0, ctx->stream);
-        for (int r = 0; r < reps; ++r)
+        float tot = 0.f;
+        for (int r = 0; r < reps; ++r) {
+            if (flush && flush_bytes) cudaMemsetAsync(flush, r & 0xff, flush_bytes, ctx->stream);
+            cudaEventRecord(t0, ctx->stream);
             run_box(p, pos, flags, min_size, reinterpret_cast<char *>(ws), label, halo_id, n_halos, st, ctx->stream);
-        cudaEventRecord(t1, ctx->stream);
-        if (cudaEventSynchronize(t1) != cudaSuccess) return -1;
-        cudaEventElapsedTime(ms, t0, t1);
-        *ms /= reps;
+            cudaEventRecord(t1, ctx->stream);
+            if (cudaEventSynchronize(t1) != cudaSuccess) return -1;
+            float one = 0.f;
+            cudaEventElapsedTime(&one, t0, t1);
+            tot += one;
+        }
+        *ms = tot / reps;
         return 0;
     };
     int rc = 0;
