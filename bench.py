@@ -63,10 +63,12 @@ LINK_PARTS = ("dense_cells", "link_medium_local", "link_small", "link_medium", "
 
 
 # DRAM traffic of the link step per launch (ncu, dram__bytes_read.sum +
-# dram__bytes_write.sum over its five launches), committed with the digest of
-# the kernel sources it was taken on: it is reported only while those sources
-# are unchanged, else null.
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_link_1024cubed.md")
+# dram__bytes_write.sum over its five launches), captured on the 256^3 box
+# (same density, linking length and halo statistics) and scaled by the 64x
+# particles of the 1024^3 box; committed with the digest of the kernel
+# sources it was taken on, and reported only while those sources are
+# unchanged, else null.
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_link_256cubed.md")
 
 
 def kernel_sources_digest():
@@ -89,7 +91,7 @@ def link_traffic():
     except OSError:
         return None
     dig = re.search(r"kernel sources sha256: ([0-9a-f]{64})", txt)
-    byt = re.search(r"link DRAM bytes per launch: ([0-9]+)", txt)
+    byt = re.search(r"link DRAM bytes per launch \(scaled to 1024\^3\): ([0-9]+)", txt)
     if not dig or not byt or dig.group(1) != kernel_sources_digest():
         return None
     return int(byt.group(1))

@@ -156,6 +156,14 @@ __global__ void __launch_bounds__(kFewThreads) bin_scatter_few_kernel(const floa
 // registers every cell with more than S particles in the medium or the dense
 // work list.
 constexpr int kSortThreads = 512;
+constexpr int kSortUnroll = 2;
+
+// Cell of a particle inside its brick (0..4095).
+__device__ __forceinline__ uint32_t local_cell(float4 q, const BinGeom &g) {
+    const int ix = cell_coord(q.x, g.inv_cell, g.n), iy = cell_coord(q.y, g.inv_cell, g.n),
+              iz = cell_coord(q.z, g.inv_cell, g.n);
+    return uint32_t(ix & 15) + 16u * (uint32_t(iy & 15) + 16u * uint32_t(iz & 15));
+}
 
 struct ClassReg {
     int S, T;                 // small: m <= S; dense: T < m <= kDenseMaxM (T = 0: none)
@@ -183,12 +191,17 @@ __global__ void __launch_bounds__(kSortThreads) brick_sort_kernel(const float4 *
         uint32_t bs = brick_start[brick * bstride], be = brick_start[(brick + 1) * bstride];
         for (int k = threadIdx.x; k < kBrickCells; k += kSortThreads) hist[k] = 0;
         __syncthreads();
-        for (uint32_t e = bs + threadIdx.x; e < be; e += kSortThreads) {
-            float4 q = tmp[e];
-            int ix = cell_coord(q.x, g.inv_cell, g.n), iy = cell_coord(q.y, g.inv_cell, g.n),
-                iz = cell_coord(q.z, g.inv_cell, g.n);
-            uint32_t lc = uint32_t(ix & 15) + 16u * (uint32_t(iy & 15) + 16u * uint32_t(iz & 15));
-            atomicAdd(&hist[lc], 1u);
+        // kSortUnroll loads in flight per thread before their counts
+        for (uint32_t e0 = bs + threadIdx.x; e0 < be; e0 += kSortUnroll * kSortThreads) {
+            float4 q[kSortUnroll];
+#pragma unroll
+            for (int u = 0; u < kSortUnroll; ++u) {
+                const uint32_t e = e0 + u * kSortThreads;
+                if (e < be) q[u] = tmp[e];
+            }
+#pragma unroll
+            for (int u = 0; u < kSortUnroll; ++u)
+                if (e0 + u * kSortThreads < be) atomicAdd(&hist[local_cell(q[u], g)], 1u);
         }
         __syncthreads();
         uint32_t v[per];
@@ -242,13 +255,20 @@ __global__ void __launch_bounds__(kSortThreads) brick_sort_kernel(const float4 *
             }
         }
         __syncthreads();
-        for (uint32_t e = bs + threadIdx.x; e < be; e += kSortThreads) {
-            float4 q = tmp[e];
-            int ix = cell_coord(q.x, g.inv_cell, g.n), iy = cell_coord(q.y, g.inv_cell, g.n),
-                iz = cell_coord(q.z, g.inv_cell, g.n);
-            uint32_t lc = uint32_t(ix & 15) + 16u * (uint32_t(iy & 15) + 16u * uint32_t(iz & 15));
-            uint32_t r = atomicAdd(&hist[lc], 1u);
-            spos[bs + r] = q;
+        for (uint32_t e0 = bs + threadIdx.x; e0 < be; e0 += kSortUnroll * kSortThreads) {
+            float4 q[kSortUnroll];
+            uint32_t r[kSortUnroll];
+#pragma unroll
+            for (int u = 0; u < kSortUnroll; ++u) {
+                const uint32_t e = e0 + u * kSortThreads;
+                if (e < be) q[u] = tmp[e];
+            }
+#pragma unroll
+            for (int u = 0; u < kSortUnroll; ++u)
+                if (e0 + u * kSortThreads < be) r[u] = atomicAdd(&hist[local_cell(q[u], g)], 1u);
+#pragma unroll
+            for (int u = 0; u < kSortUnroll; ++u)
+                if (e0 + u * kSortThreads < be) spos[bs + r[u]] = q[u];
         }
         __syncthreads();
     }
@@ -355,6 +375,26 @@ __device__ __forceinline__ bool linked(float4 p, float4 q, const LinkGeom &g) {
     return pair_d2(p, q, g.L, g.hL) <= g.b2;
 }
 
+// The same test without the minimum-image correction.  It is bit-identical
+// to linked() whenever |x_j - x_i| <= L/2 on every axis, since the
+// correction then leaves each difference unchanged: for two particles of one
+// cell when n >= 3 (cells are at most L/3 wide) and for a cell and a
+// neighbour that does not wrap around the box when n >= 5 (they lie within
+// two cells, at most 2L/5).
+__device__ __forceinline__ bool linked_near(float4 p, float4 q, const LinkGeom &g) {
+    const float dx = __fsub_rn(q.x, p.x), dy = __fsub_rn(q.y, p.y), dz = __fsub_rn(q.z, p.z);
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)) <= g.b2;
+}
+
+__device__ __forceinline__ bool linked_if(bool near, float4 p, float4 q, const LinkGeom &g) {
+    return near ? linked_near(p, q, g) : linked(p, q, g);
+}
+
+// Every neighbour of cell (cx, cy, cz) lies within the box without wrapping.
+__device__ __forceinline__ bool interior_cell(int cx, int cy, int cz, const LinkGeom &g) {
+    return g.n >= 5 && cx >= 1 && cy >= 1 && cz >= 1 && cx <= g.n - 2 && cy <= g.n - 2 && cz <= g.n - 2;
+}
+
 // Squared distance (conservative, float) from a particle to the face/edge/
 // corner a neighbour at offset o shares with its own cell c.
 __device__ __forceinline__ float gap_to_neighbour(float4 p, int cx, int cy, int cz, int ox, int oy, int oz,
@@ -416,8 +456,9 @@ __global__ void __launch_bounds__(256) small_kernel(const float4 *__restrict__ s
         uint64_t own = cell_table_index(cx, cy, cz, g.nb);
         uint32_t a1 = cell_start[own + 1];
         if (a1 - cell_start[own] > uint32_t(g.S)) continue;
+        const bool own_near = g.n >= 3;
         for (uint32_t j = uint32_t(s) + 1; j < a1; ++j)
-            if (linked(p, spos[j], g)) uf_unite(parent, int(s), int(j), st);
+            if (linked_if(own_near, p, spos[j], g)) uf_unite(parent, int(s), int(j), st);
         if (g.n < 3) continue;
         // squared gaps to the low and high faces of the cell (as in gap_to_neighbour)
         float lx = fmaxf(p.x - float(cx) * g.cell_side, 0.f), hx = fmaxf(float(cx + 1) * g.cell_side - p.x, 0.f);
@@ -444,8 +485,10 @@ __global__ void __launch_bounds__(256) small_kernel(const float4 *__restrict__ s
             uint64_t nb = cell_table_index(wrapc(cx + ox, g.n), wrapc(cy + oy, g.n), wrapc(cz + oz, g.n), g.nb);
             uint32_t b0 = cell_start[nb], b1 = cell_start[nb + 1];
             if (b1 - b0 > uint32_t(g.S)) continue;  // medium/dense neighbours handle this pair
+            const bool near = g.n >= 5 && unsigned(cx + ox) < unsigned(g.n) && unsigned(cy + oy) < unsigned(g.n) &&
+                              unsigned(cz + oz) < unsigned(g.n);
             for (uint32_t j = b0; j < b1; ++j)
-                if (linked(p, spos[j], g)) uf_unite(parent, int(s), int(j), st);
+                if (linked_if(near, p, spos[j], g)) uf_unite(parent, int(s), int(j), st);
         }
     }
 }
@@ -490,7 +533,7 @@ __device__ __forceinline__ void lunite(int *lp, int a, int b) {
 constexpr int kMedWarps = 4;  // default warps per CTA (the autotuner may pick 8)
 constexpr int kMedCap = 256;
 
-template <int W>
+template <int W, bool NEAR>
 __global__ void __launch_bounds__(32 * W) medium_local_kernel(const float4 *__restrict__ spos,
                                                                       const uint32_t *__restrict__ cell_start,
                                                                       const uint32_t *__restrict__ medium_cells,
@@ -512,7 +555,7 @@ __global__ void __launch_bounds__(32 * W) medium_local_kernel(const float4 *__re
             for (int i = 0; i < mA - 1; ++i) {
                 float4 pi = spos[a0 + i];
                 for (int j = i + 1 + lane; j < mA; j += 32)
-                    if (linked(pi, spos[a0 + j], g)) uf_unite(parent, int(a0 + i), int(a0 + j), st);
+                    if (linked_if(NEAR, pi, spos[a0 + j], g)) uf_unite(parent, int(a0 + i), int(a0 + j), st);
             }
             continue;
         }
@@ -531,7 +574,7 @@ __global__ void __launch_bounds__(32 * W) medium_local_kernel(const float4 *__re
             float4 q0 = h0 ? sp[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
             unsigned r0 = h0 ? 1u << lane : 0u;
             for (int i = 0; i < mA; ++i)
-                if (h0 && linked(sp[i], q0, g)) r0 |= 1u << i;
+                if (h0 && linked_if(NEAR, sp[i], q0, g)) r0 |= 1u << i;
             unsigned unvisited = mA == 32 ? 0xffffffffu : (1u << mA) - 1u;
             int root = 0;
             while (unvisited) {
@@ -558,8 +601,8 @@ __global__ void __launch_bounds__(32 * W) medium_local_kernel(const float4 *__re
             unsigned long long r0 = h0 ? 1ull << lane : 0ull, r1 = h1 ? 1ull << (lane + 32) : 0ull;
             for (int i = 0; i < mA; ++i) {
                 float4 pi = sp[i];
-                if (h0 && linked(pi, q0, g)) r0 |= 1ull << i;
-                if (h1 && linked(pi, q1, g)) r1 |= 1ull << i;
+                if (h0 && linked_if(NEAR, pi, q0, g)) r0 |= 1ull << i;
+                if (h1 && linked_if(NEAR, pi, q1, g)) r1 |= 1ull << i;
             }
             unsigned long long unvisited = mA == 64 ? ~0ull : (1ull << mA) - 1ull;
             int root0 = 0, root1 = 0;
@@ -607,7 +650,7 @@ __global__ void __launch_bounds__(32 * W) medium_local_kernel(const float4 *__re
                     const uint32_t bi = 1u << (i & 31);
 #pragma unroll
                     for (int h = 0; h < R; ++h)
-                        if (hv[h] && linked(pi, q[h], g)) r[h][wi] |= bi;
+                        if (hv[h] && linked_if(NEAR, pi, q[h], g)) r[h][wi] |= bi;
                 }
             }
             uint32_t unv[R];
@@ -659,7 +702,7 @@ __global__ void __launch_bounds__(32 * W) medium_local_kernel(const float4 *__re
             int iend = min(mA, cb * 32 + 32) - 1;
             for (int i = 0; i < iend; ++i) {
                 float4 pi = sp[i];
-                if (has && i < j && linked(pi, pj, g)) lunite(lp, i, j);
+                if (has && i < j && linked_if(NEAR, pi, pj, g)) lunite(lp, i, j);
             }
         }
         __syncwarp();
@@ -767,6 +810,7 @@ __global__ void __launch_bounds__(32 * W) medium_kernel(const float4 *__restrict
         const uint32_t a0 = cell_start[ga];
         const int mA = int(cell_start[ga + 1] - a0);
         if (g.n < 3) continue;
+        const bool near = interior_cell(cx, cy, cz, g);
         uint32_t nb0 = 0, nb1 = 0;
         int ncls = 0;
         if (lane < 26) {
@@ -874,7 +918,7 @@ __global__ void __launch_bounds__(32 * W) medium_kernel(const float4 *__restrict
                             [&](uint32_t t) {
                                 const int te = int(t & 255u), ta = int(t >> 8);
                                 if (repa[ta] == lrep[te]) return;
-                                if (linked(spa[ta], lq[te], g)) {
+                                if (linked_if(near, spa[ta], lq[te], g)) {
                                     const int m = uf_unite_rep(parent, int(a0) + ta, lslot[te], st);
                                     repa[ta] = m;
                                     lrep[te] = m;
@@ -921,7 +965,7 @@ __global__ void __launch_bounds__(32 * W) medium_kernel(const float4 *__restrict
                         float4 x = shfl4(pa, src);
                         int ra = ca == 0 ? __shfl_sync(0xffffffffu, rep0, src)
                                          : (ca == 32 ? __shfl_sync(0xffffffffu, rep1, src) : -3);
-                        bool join = inb && ra != repb && linked(x, qb, g);
+                        bool join = inb && ra != repb && linked_if(near, x, qb, g);
                         int merged = join ? uf_unite_rep(parent, int(a0 + ca + src), int(b0 + j), st) : 0;
                         unsigned um = __ballot_sync(0xffffffffu, join);
                         while (um) {
@@ -1045,7 +1089,7 @@ __device__ void dense_round(const uint32_t *src, int nsrc, int k, const uint16_t
                 for (int a = f0; a < f1 && !done; ++a) {
                     float4 pa = cp[a];
                     for (int cc = g0; cc < g1; ++cc) {
-                        if (linked(pa, cp[cc], g)) {
+                        if (linked_near(pa, cp[cc], g)) {  // one cell, n >= 5
                             lunite(lp, Fs, G);
                             done = true;
                             break;
@@ -1269,6 +1313,7 @@ __global__ void __launch_bounds__(32 * W) dense_nbr_kernel(const float4 *__restr
         uint32_t ga = dense_cells[d];
         int cx, cy, cz;
         decode_cell(ga, g.nb, cx, cy, cz);
+        const bool near = interior_cell(cx, cy, cz, g);
         const uint32_t a0 = cell_start[ga];
         const uint16_t *ta = sub_start + d * (kSubMax + 1);
         const uint16_t *ra = sub_rows + d * (kSubSide * kSubSide);
@@ -1319,7 +1364,7 @@ __global__ void __launch_bounds__(32 * W) dense_nbr_kernel(const float4 *__restr
                             if (uf_find(parent, qs) == uf_find(parent, int(a0 + c0))) return;
                             const float4 qq = qbuf[qi];
                             for (uint32_t cc = c0; cc < c1; ++cc)
-                                if (linked(qq, spos[a0 + cc], g)) {
+                                if (linked_if(near, qq, spos[a0 + cc], g)) {
                                     uf_unite(parent, qs, int(a0 + cc), st);
                                     break;
                                 }
@@ -1383,7 +1428,7 @@ __global__ void __launch_bounds__(32 * W) dense_nbr_kernel(const float4 *__restr
                         for (uint32_t a = f0; a < f1 && !done; ++a) {
                             const float4 p = spos[a0 + a];
                             for (uint32_t cc = c0; cc < c1; ++cc)
-                                if (linked(p, spos[b0 + cc], g)) {
+                                if (linked_if(near, p, spos[b0 + cc], g)) {
                                     uf_unite(parent, int(a0 + a), int(b0 + cc), st);
                                     done = true;
                                     break;
@@ -1450,7 +1495,9 @@ void launch_link_core(const jfof_cells &c, const FofBuffers &fb, const LinkParam
     }
     {
         JFOF_TRACE("link_medium_local", s);
-        auto k = lp.warps[0] == 8 ? medium_local_kernel<8> : medium_local_kernel<4>;
+        // pairs of one cell need no minimum image once cells are at most L/3 wide
+        auto k = c.n_axis >= 3 ? (lp.warps[0] == 8 ? medium_local_kernel<8, true> : medium_local_kernel<4, true>)
+                               : (lp.warps[0] == 8 ? medium_local_kernel<8, false> : medium_local_kernel<4, false>);
         k<<<grid_for(med_thr, 32 * lp.warps[0], 8), 32 * lp.warps[0], 0, s>>>(
             spos, c.cell_start, fb.medium_cells, fb.counters + 1, fb.counters + 3, medium_cap(N), g, fb.parent, st);
     }
