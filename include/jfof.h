@@ -90,7 +90,8 @@ int jfof_trace_enable(jfof_ctx *ctx, int on);
 int jfof_trace_read(jfof_ctx *ctx, char *buf, size_t len, size_t *written);
 
 /* Cell classes of the link step (see jfof_link): a cell with at most
-   `small_max` particles is "small" (one thread per particle); one with more
+   `small_max` particles (at most 255 is used) is "small" (its particles'
+   candidate pairs are spread over a warp); one with more
    than `dense_over` (and at most 65535) is "dense" (linked through its
    sub-cells; 0 disables that path); the rest are "medium" (one warp per
    cell).  Defaults 8 and 96.  Labels do not depend on them; only speed does.

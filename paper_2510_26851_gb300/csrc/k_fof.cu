@@ -427,69 +427,115 @@ __global__ void iota_kernel(int *__restrict__ p, int64_t N) {
 }
 
 // ---------------------------------------------------------------------------
-// Small cells: one thread per particle of a small cell (the list written by
-// the brick sort, in cell order).  Pairs with later particles of its
-// cell and with every particle of a small forward neighbour cell that lies
-// within reach (the particle's gap to that cell <= 1.02 b).  The 13 forward
-// offsets are compile-time constants here (packed 2 bits per offset and
-// axis, value + 1), so the reach test of each is two adds and a compare on the
-// particle's squared gaps to its cell's six faces.  All loops are bounded by S.
+// Small cells: a warp takes 32 consecutive entries of the list of particles of
+// small cells (written by the brick sort, in cell order).  Each lane finds its
+// particle's candidates: the later particles of its own cell and every
+// particle of a small forward neighbour cell that lies within reach (the
+// particle's gap to that cell <= 1.02 b).  The 13 forward offsets are
+// compile-time constants (packed 2 bits per offset and axis, value + 1), so
+// the reach test of each is two adds and a compare on the particle's squared
+// gaps to its cell's six faces.  The (particle, candidate) pairs of the whole
+// warp are then laid out as flat tasks (the warp task runner) and tested by
+// all lanes in turn, so no lane idles while another walks a longer list.  All
+// lists are bounded by S.
 constexpr uint32_t kFwdX = 0x2492492u, kFwdY = 0x2a540a9u, kFwdZ = 0x2aaaa55u;
+constexpr int kSmallWarps = 8;
+constexpr int kSmallTaskCap = 256;
 
 __device__ __forceinline__ int fwd_comp(uint32_t packed, int o) { return int((packed >> (2 * o)) & 3u) - 1; }
 
-__global__ void __launch_bounds__(256) small_kernel(const float4 *__restrict__ spos,
-                                                    const uint32_t *__restrict__ cell_start,
-                                                    const uint32_t *__restrict__ small_slots,
-                                                    const uint32_t *__restrict__ nsmall, uint32_t *next, LinkGeom g,
-                                                    int *parent, DevStatus st) {
-    const int lane = threadIdx.x & 31;
+template <class Emit, class Work>
+__device__ __forceinline__ void warp_tasks(int c, uint32_t *buf, int cap, int lane, Emit emit, Work work);
+
+__global__ void __launch_bounds__(32 * kSmallWarps) small_kernel(const float4 *__restrict__ spos,
+                                                                 const uint32_t *__restrict__ cell_start,
+                                                                 const uint32_t *__restrict__ small_slots,
+                                                                 const uint32_t *__restrict__ nsmall, uint32_t *next,
+                                                                 LinkGeom g, int *parent, DevStatus st) {
+    __shared__ float4 sh_p[kSmallWarps][32];
+    __shared__ int sh_s[kSmallWarps][32];
+    __shared__ uint32_t sh_near[kSmallWarps][32];
+    __shared__ uint32_t sh_start[kSmallWarps][32][14];  // [0]: own cell after the particle; [1 + o]: neighbour o
+    __shared__ uint8_t sh_cnt[kSmallWarps][32][14];
+    __shared__ uint32_t sh_task[kSmallWarps][kSmallTaskCap];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t(*start)[14] = sh_start[w];
+    uint8_t(*cnt)[14] = sh_cnt[w];
     const int64_t ns = *nsmall;
-    // a warp takes 32 consecutive entries of the list of small-cell particles
     for (int64_t c = next_task(next, lane); c * 32 < ns; c = next_task(next, lane)) {
         const int64_t t = c * 32 + lane;
-        if (t >= ns) continue;
-        const int64_t s = small_slots[t];
-        float4 p = spos[s];
-        int cx = cell_coord(p.x, g.inv_cell, g.n), cy = cell_coord(p.y, g.inv_cell, g.n),
-            cz = cell_coord(p.z, g.inv_cell, g.n);
-        uint64_t own = cell_table_index(cx, cy, cz, g.nb);
-        uint32_t a1 = cell_start[own + 1];
-        if (a1 - cell_start[own] > uint32_t(g.S)) continue;
-        const bool own_near = g.n >= 3;
-        for (uint32_t j = uint32_t(s) + 1; j < a1; ++j)
-            if (linked_if(own_near, p, spos[j], g)) uf_unite(parent, int(s), int(j), st);
-        if (g.n < 3) continue;
-        // squared gaps to the low and high faces of the cell (as in gap_to_neighbour)
-        float lx = fmaxf(p.x - float(cx) * g.cell_side, 0.f), hx = fmaxf(float(cx + 1) * g.cell_side - p.x, 0.f);
-        float ly = fmaxf(p.y - float(cy) * g.cell_side, 0.f), hy = fmaxf(float(cy + 1) * g.cell_side - p.y, 0.f);
-        float lz = fmaxf(p.z - float(cz) * g.cell_side, 0.f), hz = fmaxf(float(cz + 1) * g.cell_side - p.z, 0.f);
-        lx *= lx;
-        hx *= hx;
-        ly *= ly;
-        hy *= hy;
-        lz *= lz;
-        hz *= hz;
-        uint32_t cand = 0u;
+        int total = 0;
+        uint32_t used = 0u;  // lists with at least one candidate
+        if (t < ns) {
+            const int64_t s = small_slots[t];
+            const float4 p = spos[s];
+            const int cx = cell_coord(p.x, g.inv_cell, g.n), cy = cell_coord(p.y, g.inv_cell, g.n),
+                      cz = cell_coord(p.z, g.inv_cell, g.n);
+            const uint64_t own = cell_table_index(cx, cy, cz, g.nb);
+            const uint32_t a1 = cell_start[own + 1];
+            if (a1 - cell_start[own] <= uint32_t(g.S)) {
+                sh_p[w][lane] = p;
+                sh_s[w][lane] = int(s);
+                uint32_t nearm = g.n >= 3 ? 1u : 0u;  // pairs of one cell
+                start[lane][0] = uint32_t(s) + 1;
+                cnt[lane][0] = uint8_t(a1 - uint32_t(s) - 1);
+                total = int(a1 - uint32_t(s) - 1);
+                if (total > 0) used |= 1u;
+                if (g.n >= 3) {
+                    // squared gaps to the low and high faces of the cell (as in gap_to_neighbour)
+                    float lx = fmaxf(p.x - float(cx) * g.cell_side, 0.f), hx = fmaxf(float(cx + 1) * g.cell_side - p.x, 0.f);
+                    float ly = fmaxf(p.y - float(cy) * g.cell_side, 0.f), hy = fmaxf(float(cy + 1) * g.cell_side - p.y, 0.f);
+                    float lz = fmaxf(p.z - float(cz) * g.cell_side, 0.f), hz = fmaxf(float(cz + 1) * g.cell_side - p.z, 0.f);
+                    lx *= lx;
+                    hx *= hx;
+                    ly *= ly;
+                    hy *= hy;
+                    lz *= lz;
+                    hz *= hz;
+                    uint32_t cand = 0u;
 #pragma unroll
-        for (int o = 0; o < 13; ++o) {
-            const int ox = fwd_comp(kFwdX, o), oy = fwd_comp(kFwdY, o), oz = fwd_comp(kFwdZ, o);
-            float d = (ox > 0 ? hx : (ox < 0 ? lx : 0.f)) + (oy > 0 ? hy : (oy < 0 ? ly : 0.f)) +
-                      (oz > 0 ? hz : (oz < 0 ? lz : 0.f));
-            if (d <= g.gap2) cand |= 1u << o;
+                    for (int o = 0; o < 13; ++o) {
+                        const int ox = fwd_comp(kFwdX, o), oy = fwd_comp(kFwdY, o), oz = fwd_comp(kFwdZ, o);
+                        float d = (ox > 0 ? hx : (ox < 0 ? lx : 0.f)) + (oy > 0 ? hy : (oy < 0 ? ly : 0.f)) +
+                                  (oz > 0 ? hz : (oz < 0 ? lz : 0.f));
+                        if (d <= g.gap2) cand |= 1u << o;
+                    }
+                    while (cand) {
+                        const int o = __ffs(int(cand)) - 1;
+                        cand &= cand - 1u;
+                        const int ox = fwd_comp(kFwdX, o), oy = fwd_comp(kFwdY, o), oz = fwd_comp(kFwdZ, o);
+                        const uint64_t nb =
+                            cell_table_index(wrapc(cx + ox, g.n), wrapc(cy + oy, g.n), wrapc(cz + oz, g.n), g.nb);
+                        const uint32_t b0 = cell_start[nb], b1 = cell_start[nb + 1];
+                        if (b1 == b0 || b1 - b0 > uint32_t(g.S)) continue;  // medium/dense neighbours handle it
+                        start[lane][1 + o] = b0;
+                        cnt[lane][1 + o] = uint8_t(b1 - b0);
+                        total += int(b1 - b0);
+                        used |= 2u << o;
+                        if (g.n >= 5 && unsigned(cx + ox) < unsigned(g.n) && unsigned(cy + oy) < unsigned(g.n) &&
+                            unsigned(cz + oz) < unsigned(g.n))
+                            nearm |= 2u << o;
+                    }
+                }
+                sh_near[w][lane] = nearm;
+            }
         }
-        while (cand) {
-            const int o = __ffs(int(cand)) - 1;
-            cand &= cand - 1u;
-            const int ox = fwd_comp(kFwdX, o), oy = fwd_comp(kFwdY, o), oz = fwd_comp(kFwdZ, o);
-            uint64_t nb = cell_table_index(wrapc(cx + ox, g.n), wrapc(cy + oy, g.n), wrapc(cz + oz, g.n), g.nb);
-            uint32_t b0 = cell_start[nb], b1 = cell_start[nb + 1];
-            if (b1 - b0 > uint32_t(g.S)) continue;  // medium/dense neighbours handle this pair
-            const bool near = g.n >= 5 && unsigned(cx + ox) < unsigned(g.n) && unsigned(cy + oy) < unsigned(g.n) &&
-                              unsigned(cz + oz) < unsigned(g.n);
-            for (uint32_t j = b0; j < b1; ++j)
-                if (linked_if(near, p, spos[j], g)) uf_unite(parent, int(s), int(j), st);
-        }
+        __syncwarp();
+        // task = lane | list << 5 | index in the list << 9
+        warp_tasks(
+            total, sh_task[w], kSmallTaskCap, lane,
+            [&](auto put) {
+                for (uint32_t u = used; u; u &= u - 1u) {
+                    const int l = __ffs(int(u)) - 1;
+                    for (int k = 0; k < cnt[lane][l]; ++k) put(uint32_t(lane) | uint32_t(l) << 5 | uint32_t(k) << 9);
+                }
+            },
+            [&](uint32_t tk) {
+                const int ql = int(tk & 31u), l = int((tk >> 5) & 15u), k = int(tk >> 9);
+                const uint32_t j = start[ql][l] + uint32_t(k);
+                if (linked_if((sh_near[w][ql] >> l) & 1u, sh_p[w][ql], spos[j], g))
+                    uf_unite(parent, sh_s[w][ql], int(j), st);
+            });
     }
 }
 
@@ -1454,7 +1500,7 @@ LinkParams make_link_params(int64_t N, float L, float b, int n, int S, int T, in
     double eps = 4.0 * double(L) * std::ldexp(1.0, -24);
     bool ok = T > 0 && n >= 5 && k <= kSubSide && std::sqrt(3.0) * (sf + 2 * eps) <= double(b) * (1 - 1e-4) &&
               (double(b) + 2 * eps) / sf < 2.0;
-    lp.S = S < 0 ? 0 : S;
+    lp.S = S < 0 ? 0 : (S > kSmallMax ? kSmallMax : S);
     lp.T = ok ? (T > lp.S ? T : lp.S + 1) : 0;
     lp.k = k;
     lp.inv_fine = float(double(n) * k / double(L));
@@ -1504,7 +1550,7 @@ void launch_link_core(const jfof_cells &c, const FofBuffers &fb, const LinkParam
     // then everything that unites across cells (atomic hooks only)
     if (lp.S > 0) {
         JFOF_TRACE("link_small", s);
-        small_kernel<<<grid_for(N, 256, 8), 256, 0, s>>>(spos, c.cell_start, fb.small_slots, fb.counters + 6,
+        small_kernel<<<grid_for(N, 32 * kSmallWarps, 8), 32 * kSmallWarps, 0, s>>>(spos, c.cell_start, fb.small_slots, fb.counters + 6,
                                                           fb.counters + 7, g, fb.parent, st);
     }
     {

@@ -13,6 +13,7 @@ constexpr int kSubMax = kSubSide * kSubSide * kSubSide;  // 729
 constexpr uint32_t kDenseMaxM = 65535;
 constexpr int kDefaultDenseThreshold = 96;
 constexpr int kDefaultSmallThreshold = 8;
+constexpr int kSmallMax = 255;  // small cells hold at most this many particles
 constexpr int kCounters = 8;
 // Output-order buckets of the label scatter (at most this many).
 constexpr int kTailBuckets = 1024;
