@@ -6,10 +6,14 @@
 //   m <= 256           one warp, the segment in registers (R = P/32 values a
 //                      lane, element t = r*32 + lane): steps whose partner is
 //                      in another lane use shuffles, the others swap registers
-//   m  > 256           listed by the warp kernel, then one block per segment:
-//                      in shared memory when P <= kSegSmem, otherwise chunks of
-//                      kSegSmem sorted in shared memory and the long steps in
-//                      global memory
+//   256 < m <= 1024    listed by the warp kernel, then one warp per segment
+//                      with the segment in registers again (16 or 32 values a
+//                      lane), in a kernel of its own so the short segments keep
+//                      the smaller register footprint
+//   m  > 1024          listed too, then one block per segment: in shared
+//                      memory when P <= kSegSmem, otherwise chunks of kSegSmem
+//                      sorted in shared memory and the long steps in global
+//                      memory
 // A segment that finds the list full is sorted in place in global memory by
 // its warp (slow, but any list capacity is correct).  Used for the members
 // of each halo and for the REINFORCE pair list and its reverse adjacency.
@@ -20,6 +24,7 @@ namespace jfof {
 
 constexpr int kSegWarps = 8;
 constexpr int kSegRegMax = 256;
+constexpr int kSegMidMax = 1024;
 constexpr int kSegBlock = 256;
 constexpr int kSegSmem = 8192;
 constexpr int kSegLogSmem = 13;
@@ -163,6 +168,28 @@ __device__ void tile_store(const int32_t *b, int32_t *d, int64_t base, int64_t m
     __syncthreads();
 }
 
+// Listed segments of at most kSegMidMax members: one warp each, in registers.
+__global__ void __launch_bounds__(32 * kSegWarps) segsort_mid_kernel(const uint32_t *__restrict__ off,
+                                                                     int32_t *__restrict__ data,
+                                                                     const uint32_t *__restrict__ list,
+                                                                     int64_t list_cap) {
+    int64_t n = list[0];
+    if (n > list_cap) n = list_cap;
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t e = w0; e < n; e += nw) {
+        const uint32_t sgi = list[1 + e];
+        const uint32_t s0 = off[sgi];
+        const int m = int(off[sgi + 1] - s0);
+        if (m > kSegMidMax) continue;
+        if (m <= 512)
+            reg_sort<9>(data + s0, m, lane);
+        else
+            reg_sort<10>(data + s0, m, lane);
+    }
+}
+
 __global__ void __launch_bounds__(kSegBlock) segsort_block_kernel(const uint32_t *__restrict__ off,
                                                                   int32_t *__restrict__ data,
                                                                   const uint32_t *__restrict__ list,
@@ -175,6 +202,7 @@ __global__ void __launch_bounds__(kSegBlock) segsort_block_kernel(const uint32_t
         uint32_t sgi = list[1 + e];
         uint32_t s0 = off[sgi];
         int64_t m = int64_t(off[sgi + 1]) - int64_t(s0);
+        if (m <= kSegMidMax) continue;  // the register kernel's
         int32_t *d = data + s0;
         int lp = 0;
         while ((int64_t(1) << lp) < m) ++lp;
@@ -231,6 +259,8 @@ void launch_segsort(const uint32_t *off, int64_t S, int32_t *data, int64_t cap, 
     cudaMemsetAsync(list, 0, sizeof(uint32_t), s);
     segsort_warp_kernel<<<grid_for(S * 8, 32 * kSegWarps, 8), 32 * kSegWarps, 0, s>>>(off, S, S_dev, cap, data,
                                                                                        list, list_cap);
+    segsort_mid_kernel<<<grid_for(list_cap * 32, 32 * kSegWarps, 8), 32 * kSegWarps, 0, s>>>(off, data, list,
+                                                                                            list_cap);
     segsort_block_kernel<<<grid_for(list_cap * kSegBlock, kSegBlock, 4), kSegBlock, 0, s>>>(off, data, list,
                                                                                            list_cap);
 }
