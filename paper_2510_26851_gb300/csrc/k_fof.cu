@@ -810,14 +810,30 @@ constexpr int kMedTaskCap = 256;
 
 // Offsets o in cand whose neighbour cell p can reach (gap <= 1.02 b).
 __device__ __forceinline__ uint32_t reach_mask(float4 p, int cx, int cy, int cz, uint32_t cand, const LinkGeom &g) {
+    // squared gaps to the low and high faces of the cell; offset o and its
+    // opposite o + 13 add the gaps of the faces they cross (compile-time
+    // offsets, as in the small-cell kernel)
+    float lx = fmaxf(p.x - float(cx) * g.cell_side, 0.f), hx = fmaxf(float(cx + 1) * g.cell_side - p.x, 0.f);
+    float ly = fmaxf(p.y - float(cy) * g.cell_side, 0.f), hy = fmaxf(float(cy + 1) * g.cell_side - p.y, 0.f);
+    float lz = fmaxf(p.z - float(cz) * g.cell_side, 0.f), hz = fmaxf(float(cz + 1) * g.cell_side - p.z, 0.f);
+    lx *= lx;
+    hx *= hx;
+    ly *= ly;
+    hy *= hy;
+    lz *= lz;
+    hz *= hz;
     uint32_t m = 0u;
-    while (cand) {
-        const int o = __ffs(int(cand)) - 1;
-        cand &= cand - 1u;
-        if (gap_to_neighbour(p, cx, cy, cz, c_nb26[o][0], c_nb26[o][1], c_nb26[o][2], g.cell_side) <= g.gap2)
-            m |= 1u << o;
+#pragma unroll
+    for (int o = 0; o < 13; ++o) {
+        const int ox = fwd_comp(kFwdX, o), oy = fwd_comp(kFwdY, o), oz = fwd_comp(kFwdZ, o);
+        const float d = (ox > 0 ? hx : (ox < 0 ? lx : 0.f)) + (oy > 0 ? hy : (oy < 0 ? ly : 0.f)) +
+                        (oz > 0 ? hz : (oz < 0 ? lz : 0.f));
+        const float e = (ox > 0 ? lx : (ox < 0 ? hx : 0.f)) + (oy > 0 ? ly : (oy < 0 ? hy : 0.f)) +
+                        (oz > 0 ? lz : (oz < 0 ? hz : 0.f));
+        if (d <= g.gap2) m |= 1u << o;
+        if (e <= g.gap2) m |= 1u << (o + 13);
     }
-    return m;
+    return m & cand;
 }
 
 template <int W>
