@@ -653,6 +653,58 @@ class Batch:
         return cls(off, L, b, min_size, n_axis=n, small=S, dense=T, shape=W, device=pos.device), picks
 
 
+def _graph_ms(bt: "Batch", pos: torch.Tensor, reps: int = 3) -> float:
+    bt.run(pos, use_graph=True)
+    sync(pos.device)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        bt.run(pos, use_graph=True)
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def tune_batch(pos: torch.Tensor, box_offset, L, b, min_size: int = 20, reps: int = 3, min_gain: float = 0.01):
+    """Autotune a batch as a whole: boxes are grouped by the autotuner's size
+    bucket (round(2 log2 N), round(4 log2(L/b))) and, bucket by bucket, a
+    few candidate choices (grid, cell classes, CTA shape) are applied to all
+    of the bucket's boxes and kept only when the whole batch graph runs
+    faster.  Unlike per-box tuning this sees the boxes share the GPU and its
+    L2.  Returns (batch, per-box choices (n, S, T, shape), ms per graph)."""
+    import math
+
+    import numpy as _np
+    off = _np.ascontiguousarray(box_offset, _np.int64)
+    B = len(off) - 1
+    Ns = _np.diff(off)
+    n0 = [default_cells_per_axis(int(Ns[k]), float(L[k]), float(b[k])) for k in range(B)]
+    nmax = [max_cells_per_axis(float(L[k]), float(b[k])) for k in range(B)]
+    choice = [[n0[k], 8, 96, 0] for k in range(B)]
+    buckets = {}
+    for k in range(B):
+        key = (round(2 * math.log2(int(Ns[k]))), round(4 * math.log2(float(L[k]) / float(b[k]))))
+        buckets.setdefault(key, []).append(k)
+
+    def build(ch):
+        n, S, T, W = (list(c) for c in zip(*ch))
+        return Batch(off, L, b, min_size, n_axis=n, small=S, dense=T, shape=W, device=pos.device)
+
+    best = _graph_ms(build(choice), pos, reps)
+    cands = [(1.0, 8, 64, 0), (1.0, 8, 128, 0), (1.0, 16, 96, 0), (0.8, 8, 96, 0), (1.0, 8, 96, 1),
+             (1.0, 8, 96, 2)]
+    for key in sorted(buckets, reverse=True):  # largest boxes first
+        for f, S, T, W in cands:
+            trial = [list(c) for c in choice]
+            for k in buckets[key]:
+                n = max(3, min(nmax[k], int(round(n0[k] * f))))
+                trial[k] = [n, S, T, W]
+            ms = _graph_ms(build(trial), pos, reps)
+            if ms < best * (1.0 - min_gain):
+                best, choice = ms, trial
+    return build(choice), [tuple(c) for c in choice], best
+
+
 def set_cta_shape(shape: int = 0, device=None):
     """CTA shape of the list-driven link kernels: 0 = (4, 8, 4, 8) warps, 1 = all 8, 2 = all 4."""
     _check(library().jfof_set_cta_shape(context(device), shape), "jfof_set_cta_shape")

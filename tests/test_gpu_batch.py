@@ -134,11 +134,13 @@ def test_tuned_batch_matches_oracle(J):
         specs.append(synth.BoxSpec(f"u{k}", N, L, synth.linking_length(L, N), max(1, N // 200), 0.6, 40 + k,
                                    velocities=False))
     pos, off = make_batch(specs)
-    bt, picks = J.Batch.tuned(pos, off, [s.L for s in specs], [s.b for s in specs], min_size=20, reps=1)
-    assert len(picks) == len(specs)
-    lab, hid, nh = [t.cpu().numpy().copy() for t in bt.run(pos, use_graph=True)]
-    J.sync()
     pos_np = pos.cpu().numpy()
-    for k, sp in enumerate(specs):
-        s, e = off[k], off[k + 1]
-        check_box(J, pos_np[s:e], sp, lab[s:e], hid[s:e], nh[k])
+    bt, picks = J.Batch.tuned(pos, off, [s.L for s in specs], [s.b for s in specs], min_size=20, reps=1)
+    bt2, picks2, ms = J.tune_batch(pos, off, [s.L for s in specs], [s.b for s in specs], min_size=20, reps=1)
+    assert len(picks) == len(picks2) == len(specs) and ms > 0
+    for b_ in (bt, bt2):
+        lab, hid, nh = [t.cpu().numpy().copy() for t in b_.run(pos, use_graph=True)]
+        J.sync()
+        for k, sp in enumerate(specs):
+            s, e = off[k], off[k + 1]
+            check_box(J, pos_np[s:e], sp, lab[s:e], hid[s:e], nh[k])
