@@ -63,7 +63,7 @@ LINK_PARTS = ("dense_cells", "link_medium_local", "link_small", "link_medium", "
 
 
 # DRAM traffic of the link step per launch (ncu, dram__bytes_read.sum +
-# dram__bytes_write.sum over its five launches), captured on the 256^3 box
+# dram__bytes_write.sum over its launches), captured on the 256^3 box
 # (same density, linking length and halo statistics) and scaled by the 64x
 # particles of the 1024^3 box; committed with the digest of the kernel
 # sources it was taken on, and reported only while those sources are
@@ -338,7 +338,7 @@ def measure_batched(J, peak, reps=3):
     n0 = [J.default_cells_per_axis(sp.N, sp.L, sp.b) for sp in specs]
     choices = {}
     for p, d in zip(picks, n0):
-        key = f"n/n0={p[0] / d:.2f} S={p[1]} T={p[2]} shape={p[3]}"
+        key = f"n/n0={p[0] / d:.2f} S={p[1]} T={'auto' if p[2] < 0 else p[2]} shape={p[3]}"
         choices[key] = choices.get(key, 0) + 1
     achieved = A17_BYTES_PER_PARTICLE * N / (gt_ms * 1e-3) / 1e9
     return {"workload": "64 boxes, N log-uniform in [32^3, 192^3], L in [50, 400], seeds 0-63",

@@ -93,8 +93,9 @@ int jfof_trace_read(jfof_ctx *ctx, char *buf, size_t len, size_t *written);
    `small_max` particles (at most 255 is used) is "small" (its particles'
    candidate pairs are spread over a warp); one with more
    than `dense_over` (and at most 65535) is "dense" (linked through its
-   sub-cells; 0 disables that path); the rest are "medium" (one warp per
-   cell).  Defaults 8 and 96.  Labels do not depend on them; only speed does.
+   sub-cells; 0 disables that path; -1, the default, takes 160 for boxes of
+   more than 2^24 particles and 96 below); the rest are "medium" (one warp per
+   cell).  Default small_max 16.  Labels do not depend on them; only speed does.
    Takes effect at the next jfof_bin_cells. */
 int jfof_set_cell_classes(jfof_ctx *ctx, int32_t small_max, int32_t dense_over);
 
@@ -307,7 +308,8 @@ int jfof_fof_batched(jfof_ctx *ctx, const float *pos, const int64_t *h_box_offse
 
 /* Autotuner: times the a1-a7 pipeline on one box for candidate grids (the
    default n and n scaled by 0.8 and 1.26, where the workspace fits) and six
-   cell-class pairs with the default CTA shape, then the other CTA shapes for
+   cell-class pairs ((16, the default dense threshold), (8, 96), (16, 96),
+   (16, 128), (16, 160), (24, 128)) with the default CTA shape, then the other CTA shapes for
    the best of those, `reps` runs each after a warm-up, and returns the
    fastest choice (*best_n_axis, *best_small, *best_dense, *best_shape) and
    its time in ms.  The choice is kept in the context by size bucket

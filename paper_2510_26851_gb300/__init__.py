@@ -173,9 +173,10 @@ def set_loop_budget(iterations: int, device=None):
     _check(library().jfof_set_loop_budget(context(device), int(iterations)), "jfof_set_loop_budget")
 
 
-def set_cell_classes(small_max: int = 8, dense_over: int = 96, device=None):
+def set_cell_classes(small_max: int = 16, dense_over: int = -1, device=None):
     """Link-step cell classes: <= small_max particles "small", > dense_over
-    "dense" (sub-cell path; 0 disables it), the rest "medium"."""
+    "dense" (sub-cell path; 0 disables it; -1: 160 above 2^24 particles, 96
+    below), the rest "medium"."""
     _check(library().jfof_set_cell_classes(context(device), int(small_max), int(dense_over)),
            "jfof_set_cell_classes")
 
@@ -680,7 +681,7 @@ def tune_batch(pos: torch.Tensor, box_offset, L, b, min_size: int = 20, reps: in
     Ns = _np.diff(off)
     n0 = [default_cells_per_axis(int(Ns[k]), float(L[k]), float(b[k])) for k in range(B)]
     nmax = [max_cells_per_axis(float(L[k]), float(b[k])) for k in range(B)]
-    choice = [[n0[k], 8, 96, 0] for k in range(B)]
+    choice = [[n0[k], 16, -1, 0] for k in range(B)]
     buckets = {}
     for k in range(B):
         key = (round(2 * math.log2(int(Ns[k]))), round(4 * math.log2(float(L[k]) / float(b[k]))))
@@ -691,8 +692,8 @@ def tune_batch(pos: torch.Tensor, box_offset, L, b, min_size: int = 20, reps: in
         return Batch(off, L, b, min_size, n_axis=n, small=S, dense=T, shape=W, device=pos.device)
 
     best = _graph_ms(build(choice), pos, reps)
-    cands = [(1.0, 8, 64, 0), (1.0, 8, 128, 0), (1.0, 16, 96, 0), (0.8, 8, 96, 0), (1.0, 8, 96, 1),
-             (1.0, 8, 96, 2)]
+    cands = [(1.0, 8, 96, 0), (1.0, 16, 128, 0), (1.0, 8, 64, 0), (1.0, 24, 96, 0), (0.8, 16, -1, 0),
+             (1.0, 16, -1, 1), (1.0, 16, -1, 2)]
     for key in sorted(buckets, reverse=True):  # largest boxes first
         for f, S, T, W in cands:
             trial = [list(c) for c in choice]

@@ -42,7 +42,7 @@ int resolve_n(int64_t N, float L, float b, int32_t n_axis, int32_t *out) {
         const int32_t hi = n + (n / 8 > 2 ? n / 8 : 2);
         for (int32_t m = n; m <= hi && m <= nmax; ++m) {
             if (m < 5) break;
-            if (make_link_params(N, L, b, m, kDefaultSmallThreshold, kDefaultDenseThreshold).T > 0) {
+            if (make_link_params(N, L, b, m, kDefaultSmallThreshold, kDenseAuto).T > 0) {
                 n = m;
                 break;
             }
@@ -149,7 +149,7 @@ int jfof_create(jfof_ctx **ctx, int device, void *stream) {
     c->batch = nullptr;
     c->stream = reinterpret_cast<cudaStream_t>(stream);
     c->loop_budget = kDefaultLoopBudget;
-    c->dense_threshold = kDefaultDenseThreshold;
+    c->dense_threshold = kDenseAuto;
     c->small_threshold = kDefaultSmallThreshold;
     c->cta_shape = 0;
     c->tune = nullptr;
@@ -297,7 +297,7 @@ int jfof_set_cta_shape(jfof_ctx *ctx, int32_t shape) {
 }
 
 int jfof_set_cell_classes(jfof_ctx *ctx, int32_t small_max, int32_t dense_over) {
-    if (!ctx || small_max < 0 || dense_over < 0) return JFOF_EINVAL;
+    if (!ctx || small_max < 0 || dense_over < kDenseAuto) return JFOF_EINVAL;
     ctx->small_threshold = small_max;
     ctx->dense_threshold = dense_over;
     return JFOF_OK;

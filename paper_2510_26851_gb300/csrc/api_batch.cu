@@ -308,7 +308,8 @@ int jfof_autotune(jfof_ctx *ctx, const float *pos, int64_t N, float L, float b, 
         int n = int(n0 * f);
         if (legal(n) && n != n0) ns.push_back(n);
     }
-    const int cls[][2] = {{8, 96}, {8, 64}, {4, 96}, {8, 128}, {16, 96}, {8, 48}};
+    const int dT = default_dense_threshold(N);
+    const int cls[][2] = {{kDefaultSmallThreshold, dT}, {8, 96}, {16, 96}, {16, 128}, {16, 160}, {24, 128}};
     cudaSetDevice(ctx->device);
     cudaEvent_t t0, t1;
     if (cudaEventCreate(&t0) != cudaSuccess) return JFOF_ECUDA;
@@ -317,7 +318,7 @@ int jfof_autotune(jfof_ctx *ctx, const float *pos, int64_t N, float L, float b, 
         return JFOF_ECUDA;
     }
     float best = 1e30f;
-    int bn = n0, bS = 8, bT = 96, bW = 0;
+    int bn = n0, bS = kDefaultSmallThreshold, bT = dT, bW = 0;
     DevStatus st = ctx->dev();
     auto time_one = [&](int n, int S, int T, int W, float *ms) -> int {
         BoxPlan p = plan_box(N, L, b, n, S, T, W, min_size);

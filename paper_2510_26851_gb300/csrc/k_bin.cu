@@ -159,6 +159,7 @@ struct ClassReg {
     int64_t D_cap;
     uint32_t *medium_cells;   // [M_cap]
     uint32_t *nmedium;        // counter
+    uint32_t *nlarge;         // counter of medium cells of more than kMedMain particles
     int64_t M_cap;
     uint32_t *small_slots;    // [N] slots of the particles of small cells (null: no list)
     uint32_t *nsmall;         // counter
@@ -217,8 +218,15 @@ __global__ void __launch_bounds__(kSortThreads) brick_sort_kernel(const float4 *
                     }
                 }
                 if (!dense) {
-                    uint32_t id = atomicAdd(cr.nmedium, 1u);
-                    if (int64_t(id) < cr.M_cap) cr.medium_cells[id] = uint32_t(gidx);
+                    // medium cells from the front of the array, large ones from
+                    // its back (together at most one per non-empty cell < M_cap)
+                    if (v[k] <= uint32_t(kMedMain)) {
+                        uint32_t id = atomicAdd(cr.nmedium, 1u);
+                        if (int64_t(id) < cr.M_cap) cr.medium_cells[id] = uint32_t(gidx);
+                    } else {
+                        uint32_t id = atomicAdd(cr.nlarge, 1u);
+                        if (int64_t(id) < cr.M_cap) cr.medium_cells[cr.M_cap - 1 - int64_t(id)] = uint32_t(gidx);
+                    }
                 }
             }
         }
@@ -304,8 +312,18 @@ void launch_bin_cells(const float *pos, int64_t N, float L, int n, bool wrap, co
             bin_scatter_kernel<<<grid_for(N, 256), 256, 0, s>>>(pos, N, g, fb.cursor, fb.tmp, st);
         }
     }
-    ClassReg cr{lp.S, lp.T, fb.dense_id, fb.dense_cells, fb.counters, lp.D_cap, fb.medium_cells, fb.counters + 1,
-                medium_cap(N), lp.S < INT32_MAX ? fb.small_slots : nullptr, fb.counters + 6};
+    ClassReg cr{lp.S,
+                lp.T,
+                fb.dense_id,
+                fb.dense_cells,
+                fb.counters,
+                lp.D_cap,
+                fb.medium_cells,
+                fb.counters + 1,
+                fb.counters + 8,
+                medium_cap(N),
+                lp.S < INT32_MAX ? fb.small_slots : nullptr,
+                fb.counters + 6};
     {
         JFOF_TRACE("brick_sort", s);
         brick_sort_kernel<<<grid_for(n_bricks * kSortThreads, kSortThreads, 4), kSortThreads, 0, s>>>(

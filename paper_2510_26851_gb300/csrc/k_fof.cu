@@ -268,19 +268,106 @@ __device__ __forceinline__ void lunite(int *lp, int a, int b) {
 }
 
 // ---------------------------------------------------------------------------
+// Components of a cell of at most 32 R particles (staged in sp): lane owns
+// particles lane + 32 h (h < R) and their adjacency masks of R 32-bit words
+// (word indices are compile-time constants, so the masks stay in registers);
+// every pair is tested with the exact predicate.  Components by breadth-first
+// search from the lowest unvisited particle: a frontier step is one warp
+// OR-reduction per word, and the seed is the component's smallest local
+// index.  Writes parent[a0 + i] = a0 + seed of i's component.
+template <int R, bool NEAR>
+__device__ __forceinline__ void local_bitmask(const float4 *sp, int mA, uint32_t a0, int lane, const LinkGeom &g,
+                                              int *parent) {
+    float4 q[R];
+    bool hv[R];
+    uint32_t r[R][R];
+#pragma unroll
+    for (int h = 0; h < R; ++h) {
+        hv[h] = lane + 32 * h < mA;
+        q[h] = hv[h] ? sp[lane + 32 * h] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int wd = 0; wd < R; ++wd) r[h][wd] = (hv[h] && wd == h) ? 1u << lane : 0u;
+    }
+#pragma unroll
+    for (int wi = 0; wi < R; ++wi) {
+        const int iend = min(mA, 32 * wi + 32);
+        for (int i = 32 * wi; i < iend; ++i) {
+            const float4 pi = sp[i];
+            const uint32_t bi = 1u << (i & 31);
+#pragma unroll
+            for (int h = 0; h < R; ++h)
+                if (hv[h] && linked_if(NEAR, pi, q[h], g)) r[h][wi] |= bi;
+        }
+    }
+    uint32_t unv[R];
+    int root[R];
+#pragma unroll
+    for (int wd = 0; wd < R; ++wd) {
+        const int c = min(max(mA - 32 * wd, 0), 32);
+        unv[wd] = c == 32 ? 0xffffffffu : (1u << c) - 1u;
+        root[wd] = 0;
+    }
+    while (true) {
+        int sw = -1;
+        uint32_t su = 0u;
+#pragma unroll
+        for (int wd = R - 1; wd >= 0; --wd)
+            if (unv[wd]) {
+                sw = wd;
+                su = unv[wd];
+            }
+        if (sw < 0) break;
+        const int sb = __ffs(int(su)) - 1, seed = 32 * sw + sb;
+        uint32_t comp[R], fr[R];
+#pragma unroll
+        for (int wd = 0; wd < R; ++wd) comp[wd] = fr[wd] = wd == sw ? 1u << sb : 0u;
+        while (true) {
+            uint32_t any = 0u;
+#pragma unroll
+            for (int wd = 0; wd < R; ++wd) any |= fr[wd];
+            if (!any) break;
+            uint32_t nb[R];
+#pragma unroll
+            for (int wd = 0; wd < R; ++wd) {
+                uint32_t v = 0u;
+#pragma unroll
+                for (int h = 0; h < R; ++h)
+                    if ((fr[h] >> lane) & 1u) v |= r[h][wd];
+                nb[wd] = __reduce_or_sync(0xffffffffu, v);
+            }
+#pragma unroll
+            for (int wd = 0; wd < R; ++wd) {
+                fr[wd] = nb[wd] & ~comp[wd];
+                comp[wd] |= nb[wd];
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < R; ++h) {
+            if ((comp[h] >> lane) & 1u) root[h] = seed;
+            unv[h] &= ~comp[h];
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < R; ++h)
+        if (hv[h]) parent[a0 + lane + 32 * h] = int(a0) + root[h];
+}
+
 // Medium cells, local part: one warp per cell.  The cell's particles are
 // staged in shared memory and all their pairs tested (lane = one particle,
-// the other broadcast).  Up to 96 particles: adjacency bitmasks and a
+// the other broadcast).  Up to kMedBig particles: adjacency bitmasks and a
 // breadth-first search over them; larger cells: a shared-memory union-find
 // over local indices.  Then parent[slot] = first slot of the slot's local
 // component.  A cell larger than the staging area (possible only when it
 // cannot take the dense path) links its own pairs through the global forest
-// instead.  Runs before any kernel that unites across cells, since it writes
-// parent with plain stores.
+// instead.  Cells of at most kMedMain particles come from the front of the
+// medium-cell array (LARGE false), larger ones from its back (LARGE true), so
+// each instance keeps the registers of its own sizes.
+// Runs before any kernel that unites across cells, since it writes parent
+// with plain stores.
 constexpr int kMedWarps = 4;  // default warps per CTA (the autotuner may pick 8)
 constexpr int kMedCap = 256;
 
-template <int W, bool NEAR>
+template <int W, bool NEAR, bool LARGE>
 __global__ void __launch_bounds__(32 * W) medium_local_kernel(const float4 *__restrict__ spos,
                                                                       const uint32_t *__restrict__ cell_start,
                                                                       const uint32_t *__restrict__ medium_cells,
@@ -295,7 +382,7 @@ __global__ void __launch_bounds__(32 * W) medium_local_kernel(const float4 *__re
     int64_t M = *nmedium;
     if (M > M_cap) M = M_cap;
     for (int64_t t = next_task(next, lane); t < M; t = next_task(next, lane)) {
-        uint32_t ga = medium_cells[t];
+        uint32_t ga = medium_cells[LARGE ? M_cap - 1 - t : t];
         uint32_t a0 = cell_start[ga];
         int mA = int(cell_start[ga + 1] - a0);
         if (mA > kMedCap) {
@@ -311,7 +398,7 @@ __global__ void __launch_bounds__(32 * W) medium_local_kernel(const float4 *__re
             lp[q] = q;
         }
         __syncwarp();
-        if (mA <= 32) {
+        if (!LARGE && mA <= 32) {
             // One particle per lane: its 32-bit adjacency mask (every pair
             // tested with the exact predicate).  Components by breadth-first
             // search from the lowest unvisited particle: a frontier step is one
@@ -339,7 +426,7 @@ __global__ void __launch_bounds__(32 * W) medium_local_kernel(const float4 *__re
             __syncwarp();
             continue;
         }
-        if (mA <= 64) {
+        if (!LARGE && mA <= 64) {
             // The same for up to 64 particles: each lane owns particles lane
             // and lane+32 and their 64-bit adjacency masks.
             const bool h0 = lane < mA, h1 = lane + 32 < mA;
@@ -374,71 +461,18 @@ __global__ void __launch_bounds__(32 * W) medium_local_kernel(const float4 *__re
             __syncwarp();
             continue;
         }
-        if (mA <= 96) {
-            // The same for up to 96 particles: particles lane, lane+32 and
-            // lane+64, with 96-bit masks in three words (word indices are
-            // compile-time constants, so the masks stay in registers).
-            constexpr int R = 3;
-            float4 q[R];
-            bool hv[R];
-            uint32_t r[R][R];
-#pragma unroll
-            for (int h = 0; h < R; ++h) {
-                hv[h] = lane + 32 * h < mA;
-                q[h] = hv[h] ? sp[lane + 32 * h] : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                for (int wd = 0; wd < R; ++wd) r[h][wd] = (hv[h] && wd == h) ? 1u << lane : 0u;
-            }
-#pragma unroll
-            for (int wi = 0; wi < R; ++wi) {
-                const int iend = min(mA, 32 * wi + 32);
-                for (int i = 32 * wi; i < iend; ++i) {
-                    const float4 pi = sp[i];
-                    const uint32_t bi = 1u << (i & 31);
-#pragma unroll
-                    for (int h = 0; h < R; ++h)
-                        if (hv[h] && linked_if(NEAR, pi, q[h], g)) r[h][wi] |= bi;
-                }
-            }
-            uint32_t unv[R];
-#pragma unroll
-            for (int wd = 0; wd < R; ++wd) {
-                const int c = min(max(mA - 32 * wd, 0), 32);
-                unv[wd] = c == 32 ? 0xffffffffu : (1u << c) - 1u;
-            }
-            int root[R] = {0, 0, 0};
-            while (unv[0] | unv[1] | unv[2]) {
-                const int sw = unv[0] ? 0 : (unv[1] ? 1 : 2);
-                const uint32_t su = sw == 0 ? unv[0] : (sw == 1 ? unv[1] : unv[2]);
-                const int sb = __ffs(int(su)) - 1, seed = 32 * sw + sb;
-                uint32_t comp[R], fr[R];
-#pragma unroll
-                for (int wd = 0; wd < R; ++wd) comp[wd] = fr[wd] = wd == sw ? 1u << sb : 0u;
-                while (fr[0] | fr[1] | fr[2]) {
-                    uint32_t nb[R];
-#pragma unroll
-                    for (int wd = 0; wd < R; ++wd) {
-                        uint32_t v = 0u;
-#pragma unroll
-                        for (int h = 0; h < R; ++h)
-                            if ((fr[h] >> lane) & 1u) v |= r[h][wd];
-                        nb[wd] = __reduce_or_sync(0xffffffffu, v);
-                    }
-#pragma unroll
-                    for (int wd = 0; wd < R; ++wd) {
-                        fr[wd] = nb[wd] & ~comp[wd];
-                        comp[wd] |= nb[wd];
-                    }
-                }
-#pragma unroll
-                for (int h = 0; h < R; ++h) {
-                    if ((comp[h] >> lane) & 1u) root[h] = seed;
-                    unv[h] &= ~comp[h];
-                }
-            }
-#pragma unroll
-            for (int h = 0; h < R; ++h)
-                if (hv[h]) parent[a0 + lane + 32 * h] = int(a0) + root[h];
+        if (!LARGE && mA <= kMedMain) {
+            local_bitmask<3, NEAR>(sp, mA, a0, lane, g, parent);
+            __syncwarp();
+            continue;
+        }
+        if (LARGE && mA <= 128) {
+            local_bitmask<4, NEAR>(sp, mA, a0, lane, g, parent);
+            __syncwarp();
+            continue;
+        }
+        if (LARGE && mA <= kMedBig) {
+            local_bitmask<5, NEAR>(sp, mA, a0, lane, g, parent);
             __syncwarp();
             continue;
         }
@@ -495,19 +529,20 @@ struct SubBox {
 // neighbour (any direction) or a medium forward neighbour that lies within
 // reach of A is gathered, with the offset of its cell, into a shared-memory
 // list (the neighbours' particles are spread over the lanes as one flat
-// range); the list is then swept as flat (entry, particle of A) tasks over
-// the particles of A that reach the entry's offset (a 26-bit reach mask per
-// particle, and per offset the set of particles that reach it).  Cached
+// range); the list is then swept one entry per lane over the particles of A
+// that reach the entry's offset (a 26-bit reach mask per particle, and per
+// offset the set of particles that reach it).  Cached
 // component representatives (one per particle of A, one per entry): a value
 // is always a node that was in the entity's component at some time, so equal
 // values mean one component and such a linked pair needs no union; a union
 // stores the merged representative on both sides (a stale value only costs
-// an exact union).  A cell of more than 96 particles (possible only when it
-// cannot take the dense path) walks its neighbours one at a time instead.
+// an exact union).  Cells of at most kMedMain particles come from the front of
+// the medium-cell array (LARGE false: reach sets of 3 words), larger ones from
+// its back (LARGE true: 5 words, up to kMedBig particles); a cell larger than
+// that (possible only when it cannot take the dense path) walks its
+// neighbours one at a time instead.
 constexpr int kMedXWarps = 8;  // default warps per CTA (the autotuner may pick 4)
 constexpr int kMedList = 64;
-constexpr int kMedA = 96;        // cells up to this size take the list path
-constexpr int kMedTaskCap = 256;
 
 // Offsets o in cand whose neighbour cell p can reach (gap <= 1.02 b).
 __device__ __forceinline__ uint32_t reach_mask(float4 p, int cx, int cy, int cz, uint32_t cand, const LinkGeom &g) {
@@ -537,7 +572,7 @@ __device__ __forceinline__ uint32_t reach_mask(float4 p, int cx, int cy, int cz,
     return m & cand;
 }
 
-template <int W>
+template <int W, bool LARGE>
 __global__ void __launch_bounds__(32 * W) medium_kernel(const float4 *__restrict__ spos,
                                                                  const uint32_t *__restrict__ cell_start,
                                                                  const uint32_t *__restrict__ medium_cells,
@@ -550,24 +585,24 @@ __global__ void __launch_bounds__(32 * W) medium_kernel(const float4 *__restrict
     __shared__ int sh_slot[W][kMedList];
     __shared__ int sh_rep[W][kMedList];
     __shared__ int sh_pre[W][32];
-    __shared__ float4 sh_pa[W][kMedA];
-    __shared__ int sh_repa[W][kMedA];
-    __shared__ uint32_t sh_amask[W][26][3];
-    __shared__ uint32_t sh_task[W][kMedTaskCap];
+    constexpr int R = LARGE ? 5 : 3;                    // words of a reach set
+    constexpr int LIM = LARGE ? kMedBig : kMedMain;     // cells the list path takes
+    __shared__ float4 sh_pa[W][LIM];
+    __shared__ int sh_repa[W][LIM];
+    __shared__ uint32_t sh_amask[W][26][R];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     float4 *lq = sh_q[w];
     int *lslot = sh_slot[w], *lrep = sh_rep[w], *pre = sh_pre[w];
     float4 *spa = sh_pa[w];
     int *repa = sh_repa[w];
-    uint32_t(*amask)[3] = sh_amask[w];
-    uint32_t *tasks = sh_task[w];
+    uint32_t(*amask)[R] = sh_amask[w];
     // this lane's neighbour offset (lanes < 26), packed for shuffles
     const int my_off = lane < 26 ? (c_nb26[lane][0] + 1) | (c_nb26[lane][1] + 1) << 2 | (c_nb26[lane][2] + 1) << 4
                                  : 0;
     int64_t M = *nmedium;
     if (M > M_cap) M = M_cap;
     for (int64_t t = next_task(next, lane); t < M; t = next_task(next, lane)) {
-        uint32_t ga = medium_cells[t];
+        uint32_t ga = medium_cells[LARGE ? M_cap - 1 - t : t];
         int cx, cy, cz;
         decode_cell(ga, g.nb, cx, cy, cz);
         const uint32_t a0 = cell_start[ga];
@@ -585,40 +620,32 @@ __global__ void __launch_bounds__(32 * W) medium_kernel(const float4 *__restrict
         }
         int rep0 = lane < mA ? uf_find(parent, int(a0 + lane)) : -1;
         int rep1 = lane + 32 < mA ? uf_find(parent, int(a0 + lane + 32)) : -1;
-        if (mA <= kMedA) {
-            int rep2 = lane + 64 < mA ? uf_find(parent, int(a0 + lane + 64)) : -1;
-            const float4 pa0 = lane < mA ? spos[a0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4 pa1 = lane + 32 < mA ? spos[a0 + lane + 32] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4 pa2 = lane + 64 < mA ? spos[a0 + lane + 64] : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (mA <= LIM) {
             // neighbours to visit: small cells all round, medium forward
             const uint32_t cand = __ballot_sync(0xffffffffu, lane < 26 && (ncls == 1 || (ncls == 2 && lane < 13)));
-            const uint32_t m0 = lane < mA ? reach_mask(pa0, cx, cy, cz, cand, g) : 0u;
-            const uint32_t m1 = lane + 32 < mA ? reach_mask(pa1, cx, cy, cz, cand, g) : 0u;
-            const uint32_t m2 = lane + 64 < mA ? reach_mask(pa2, cx, cy, cz, cand, g) : 0u;
-            const uint32_t reach = __reduce_or_sync(0xffffffffu, m0 | m1 | m2);
-            // the cell's particles, their representatives, and per offset the set
-            // of particles that reach it (three 32-bit words)
-            if (lane < mA) {
-                spa[lane] = pa0;
-                repa[lane] = rep0;
+            // the cell's particles, their representatives, their reach masks, and
+            // per offset the set of particles that reach it (R 32-bit words)
+            uint32_t mm[R];
+            uint32_t any = 0u;
+#pragma unroll
+            for (int h = 0; h < R; ++h) {
+                const bool in = lane + 32 * h < mA;
+                const int rp = h == 0 ? rep0 : (h == 1 ? rep1 : (in ? uf_find(parent, int(a0 + lane + 32 * h)) : -1));
+                const float4 pa = in ? spos[a0 + lane + 32 * h] : make_float4(0.f, 0.f, 0.f, 0.f);
+                mm[h] = in ? reach_mask(pa, cx, cy, cz, cand, g) : 0u;
+                any |= mm[h];
+                if (in) {
+                    spa[lane + 32 * h] = pa;
+                    repa[lane + 32 * h] = rp;
+                }
             }
-            if (lane + 32 < mA) {
-                spa[lane + 32] = pa1;
-                repa[lane + 32] = rep1;
-            }
-            if (lane + 64 < mA) {
-                spa[lane + 64] = pa2;
-                repa[lane + 64] = rep2;
-            }
+            const uint32_t reach = __reduce_or_sync(0xffffffffu, any);
             for (uint32_t rb = reach; rb; rb &= rb - 1u) {
                 const int o = __ffs(int(rb)) - 1;
-                const uint32_t w0 = __ballot_sync(0xffffffffu, (m0 >> o) & 1u);
-                const uint32_t w1 = __ballot_sync(0xffffffffu, (m1 >> o) & 1u);
-                const uint32_t w2 = __ballot_sync(0xffffffffu, (m2 >> o) & 1u);
-                if (lane == 0) {
-                    amask[o][0] = w0;
-                    amask[o][1] = w1;
-                    amask[o][2] = w2;
+#pragma unroll
+                for (int h = 0; h < R; ++h) {
+                    const uint32_t wv = __ballot_sync(0xffffffffu, (mm[h] >> o) & 1u);
+                    if (lane == 0) amask[o][h] = wv;
                 }
             }
             const bool take = (reach >> lane) & 1u;
@@ -662,31 +689,38 @@ __global__ void __launch_bounds__(32 * W) medium_kernel(const float4 *__restrict
                 nl += __popc(bal);
                 __syncwarp();
                 if (nl > kMedList - 32 || (t0 + 32 >= total && nl > 0)) {
-                    // sweep the list as flat (entry, particle of A) tasks: only the
-                    // particles of A that reach the entry's offset
+                    // sweep the list: each entry against the particles of A that
+                    // reach its offset
                     for (int e = lane; e < nl; e += 32) lrep[e] = uf_find(parent, lslot[e]);
                     __syncwarp();
-                    for (int eb = 0; eb < nl; eb += 32) {
-                        const int e = eb + lane;
-                        const int oe = e < nl ? __float_as_int(lq[e].w) : 0;
-                        const int ce = e < nl ? __popc(amask[oe][0]) + __popc(amask[oe][1]) + __popc(amask[oe][2]) : 0;
-                        warp_tasks(
-                            ce, tasks, kMedTaskCap, lane,
-                            [&](auto put) {
+                    // One entry per lane, its reaching particles in turn: once
+                    // the entry has joined a component, the particles of A
+                    // already known to be in it cost one comparison each
+                    // (their cached representative equals the entry's, or one
+                    // of the last representatives the entry's unions merged
+                    // away).  Flat (entry, particle) tasks spread over the lanes
+                    // tested many pairs of one entry at once, before any link
+                    // of that entry was visible.
+                    for (int e = lane; e < nl; e += 32) {
+                        const int oe = __float_as_int(lq[e].w);
+                        const float4 qe = lq[e];
+                        int re = lrep[e], al0 = -1, al1 = -1, al2 = -1;
 #pragma unroll
-                                for (int wd = 0; wd < 3; ++wd)
-                                    for (uint32_t bits = amask[oe][wd]; bits; bits &= bits - 1u)
-                                        put(uint32_t(e) | uint32_t(32 * wd + __ffs(int(bits)) - 1) << 8);
-                            },
-                            [&](uint32_t t) {
-                                const int te = int(t & 255u), ta = int(t >> 8);
-                                if (repa[ta] == lrep[te]) return;
-                                if (linked_if(near, spa[ta], lq[te], g)) {
-                                    const int m = uf_unite_rep(parent, int(a0) + ta, lslot[te], st);
+                        for (int wd = 0; wd < R; ++wd)
+                            for (uint32_t bits = amask[oe][wd]; bits; bits &= bits - 1u) {
+                                const int ta = 32 * wd + __ffs(int(bits)) - 1;
+                                const int ra = repa[ta];
+                                if (ra == re || ra == al0 || ra == al1 || ra == al2) continue;
+                                if (linked_if(near, spa[ta], qe, g)) {
+                                    const int m = uf_unite_rep(parent, int(a0) + ta, lslot[e], st);
                                     repa[ta] = m;
-                                    lrep[te] = m;
+                                    al2 = al1;
+                                    al1 = ra;
+                                    al0 = re;
+                                    re = m;
                                 }
-                            });
+                            }
+                        lrep[e] = re;
                     }
                     __syncwarp();
                     nl = 0;
@@ -1207,6 +1241,7 @@ __global__ void __launch_bounds__(32 * W) dense_nbr_kernel(const float4 *__restr
 // ---------------------------------------------------------------------------
 LinkParams make_link_params(int64_t N, float L, float b, int n, int S, int T, int shape) {
     LinkParams lp{};
+    if (T < 0) T = default_dense_threshold(N);
     const int w[3][4] = {{kMedWarps, kMedXWarps, kDenseWarps, kNbrWarps}, {8, 8, 8, 8}, {4, 4, 4, 4}};
     const int sh = shape >= 0 && shape < kCtaShapes ? shape : 0;
     for (int q = 0; q < 4; ++q) lp.warps[q] = w[sh][q];
@@ -1242,12 +1277,14 @@ void launch_link_core(const jfof_cells &c, const FofBuffers &fb, const LinkParam
         return (w < cap ? w : cap) * 32;
     };
     const int64_t med_thr = list_threads(medium_cap(N), lp.S + 1), dense_thr = list_threads(lp.D_cap, lp.T + 1);
+    const int64_t big_thr = list_threads(medium_cap(N), kMedMain + 1);
     {
         JFOF_TRACE("link_init", s);
         iota_kernel<<<grid_for(N, 256), 256, 0, s>>>(fb.parent, N);
     }
     cudaMemsetAsync(fb.counters + 2, 0, 4 * sizeof(uint32_t), s);  // work counters
     cudaMemsetAsync(fb.counters + 7, 0, sizeof(uint32_t), s);
+    cudaMemsetAsync(fb.counters + 9, 0, 2 * sizeof(uint32_t), s);
     // local passes first: they write parent with plain stores, each for its own cell
     if (lp.T > 0) {
         JFOF_TRACE("dense_cells", s);
@@ -1259,10 +1296,15 @@ void launch_link_core(const jfof_cells &c, const FofBuffers &fb, const LinkParam
     {
         JFOF_TRACE("link_medium_local", s);
         // pairs of one cell need no minimum image once cells are at most L/3 wide
-        auto k = c.n_axis >= 3 ? (lp.warps[0] == 8 ? medium_local_kernel<8, true> : medium_local_kernel<4, true>)
-                               : (lp.warps[0] == 8 ? medium_local_kernel<8, false> : medium_local_kernel<4, false>);
+        const bool W8 = lp.warps[0] == 8, nr = c.n_axis >= 3;
+        auto k = nr ? (W8 ? medium_local_kernel<8, true, false> : medium_local_kernel<4, true, false>)
+                    : (W8 ? medium_local_kernel<8, false, false> : medium_local_kernel<4, false, false>);
         k<<<grid_for(med_thr, 32 * lp.warps[0], 8), 32 * lp.warps[0], 0, s>>>(
             spos, c.cell_start, fb.medium_cells, fb.counters + 1, fb.counters + 3, medium_cap(N), g, fb.parent, st);
+        auto kb = nr ? (W8 ? medium_local_kernel<8, true, true> : medium_local_kernel<4, true, true>)
+                     : (W8 ? medium_local_kernel<8, false, true> : medium_local_kernel<4, false, true>);
+        kb<<<grid_for(big_thr, 32 * lp.warps[0], 8), 32 * lp.warps[0], 0, s>>>(
+            spos, c.cell_start, fb.medium_cells, fb.counters + 8, fb.counters + 9, medium_cap(N), g, fb.parent, st);
     }
     // then everything that unites across cells (atomic hooks only)
     if (lp.S > 0) {
@@ -1272,9 +1314,13 @@ void launch_link_core(const jfof_cells &c, const FofBuffers &fb, const LinkParam
     }
     {
         JFOF_TRACE("link_medium", s);
-        auto k = lp.warps[1] == 4 ? medium_kernel<4> : medium_kernel<8>;
+        auto k = lp.warps[1] == 4 ? medium_kernel<4, false> : medium_kernel<8, false>;
         k<<<grid_for(med_thr, 32 * lp.warps[1], 8), 32 * lp.warps[1], 0, s>>>(
             spos, c.cell_start, fb.medium_cells, fb.counters + 1, fb.counters + 4, fb.dense_id, medium_cap(N), g,
+            fb.parent, st);
+        auto kb = lp.warps[1] == 4 ? medium_kernel<4, true> : medium_kernel<8, true>;
+        kb<<<grid_for(big_thr, 32 * lp.warps[1], 8), 32 * lp.warps[1], 0, s>>>(
+            spos, c.cell_start, fb.medium_cells, fb.counters + 8, fb.counters + 10, fb.dense_id, medium_cap(N), g,
             fb.parent, st);
     }
     if (lp.T > 0) {

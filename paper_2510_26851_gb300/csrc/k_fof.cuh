@@ -11,10 +11,23 @@ namespace jfof {
 constexpr int kSubSide = 9;
 constexpr int kSubMax = kSubSide * kSubSide * kSubSide;  // 729
 constexpr uint32_t kDenseMaxM = 65535;
-constexpr int kDefaultDenseThreshold = 96;
-constexpr int kDefaultSmallThreshold = 8;
+// Dense threshold when none is set (kDenseAuto): 160 for boxes of more than
+// 2^24 particles, where it measured fastest; 96 below, where a box's time is
+// set by its slowest cells and a large medium cell takes longer than the
+// dense path for it.
+constexpr int kDenseAuto = -1;
+inline int default_dense_threshold(int64_t N) { return N > (int64_t(1) << 24) ? 160 : 96; }
+constexpr int kDefaultSmallThreshold = 16;
 constexpr int kSmallMax = 255;  // small cells hold at most this many particles
-constexpr int kCounters = 8;
+// Medium cells (more than S particles, not on the dense path) are listed in
+// one array: cells of at most kMedMain particles from its front, larger ones
+// from its back.  Up to kMedBig particles their pairs are found through
+// adjacency bitmasks and reach sets of 32-bit words.
+constexpr int kMedMain = 96;
+constexpr int kMedBig = 160;
+// dense cells, medium cells, four work counters, small-cell particles, small
+// work counter, large medium cells, two work counters
+constexpr int kCounters = 12;
 // Output-order buckets of the label scatter (at most this many).
 constexpr int kTailBuckets = 1024;
 // Binning of grids with at most kFewBricks bricks: a counting sort by
@@ -45,11 +58,12 @@ struct FofBuffers {
     uint32_t *dense_id;    // [cell table]
     uint32_t *dense_cells; // [D_cap]
     uint32_t *counters;    // [kCounters]: dense cells, medium cells, four work counters,
-                           // small-cell particles, small work counter
+                           // small-cell particles, small work counter, large medium
+                           // cells, their two work counters
     uint32_t *small_slots; // [N] slots of the particles of small cells
     uint16_t *sub_start;   // [D_cap][kSubMax + 1]
     uint16_t *sub_rows;    // [D_cap][kSubSide^2] bit x of row (y, z): sub-cell non-empty
-    uint32_t *medium_cells;// [medium_cap]
+    uint32_t *medium_cells;// [medium_cap] medium cells from the front, large ones from the back
     uint32_t *bucket_fill; // [kTailBuckets] label-scatter bucket cursors
     uint32_t *bin_mat;     // [kFewGrid][bricks] per-CTA brick counts (few-brick grids)
     uint32_t *bin_base;    // [bricks * kFewGrid + 1] their brick-major exclusive scan
