@@ -94,7 +94,7 @@ int jfof_trace_read(jfof_ctx *ctx, char *buf, size_t len, size_t *written);
    candidate pairs are spread over a warp); one with more
    than `dense_over` (and at most 65535) is "dense" (linked through its
    sub-cells; 0 disables that path; -1, the default, takes 160 for boxes of
-   more than 2^24 particles and 96 below); the rest are "medium" (one warp per
+   more than 2^23 particles and 96 below); the rest are "medium" (one warp per
    cell).  Default small_max 16.  Labels do not depend on them; only speed does.
    Takes effect at the next jfof_bin_cells. */
 int jfof_set_cell_classes(jfof_ctx *ctx, int32_t small_max, int32_t dense_over);

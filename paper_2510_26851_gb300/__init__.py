@@ -175,7 +175,7 @@ def set_loop_budget(iterations: int, device=None):
 
 def set_cell_classes(small_max: int = 16, dense_over: int = -1, device=None):
     """Link-step cell classes: <= small_max particles "small", > dense_over
-    "dense" (sub-cell path; 0 disables it; -1: 160 above 2^24 particles, 96
+    "dense" (sub-cell path; 0 disables it; -1: 160 above 2^23 particles, 96
     below), the rest "medium"."""
     _check(library().jfof_set_cell_classes(context(device), int(small_max), int(dense_over)),
            "jfof_set_cell_classes")

@@ -12,11 +12,11 @@ constexpr int kSubSide = 9;
 constexpr int kSubMax = kSubSide * kSubSide * kSubSide;  // 729
 constexpr uint32_t kDenseMaxM = 65535;
 // Dense threshold when none is set (kDenseAuto): 160 for boxes of more than
-// 2^24 particles, where it measured fastest; 96 below, where a box's time is
-// set by its slowest cells and a large medium cell takes longer than the
-// dense path for it.
+// 2^23 particles, where it measured fastest; 96 below (the boxes of a batch),
+// where a box's time is set by its slowest cells and a large medium cell
+// takes longer than the dense path for it.
 constexpr int kDenseAuto = -1;
-inline int default_dense_threshold(int64_t N) { return N > (int64_t(1) << 24) ? 160 : 96; }
+inline int default_dense_threshold(int64_t N) { return N > (int64_t(1) << 23) ? 160 : 96; }
 constexpr int kDefaultSmallThreshold = 16;
 constexpr int kSmallMax = 255;  // small cells hold at most this many particles
 // Medium cells (more than S particles, not on the dense path) are listed in
