@@ -110,8 +110,16 @@ def test_labels_invariant_across_cell_classes(J, boost):
     pos, _ = synth.generate(spec, device="cuda", velocities=False)
     pos_np = pos.cpu().numpy()
     lab_ref = oracle.fof_labels(pos_np, spec.L, spec.b)
+    n = J.default_cells_per_axis(spec.N, spec.L, spec.b)
+    ic = np.minimum((pos_np.astype(np.float64) * (n / spec.L)).astype(np.int64), n - 1)
+    m = np.bincount(ic[:, 0] + n * (ic[:, 1] + n * ic[:, 2]), minlength=n ** 3)
+    assert ((m > 96) & (m <= 160)).any() and (m > 160).any()  # both large-medium paths are used
     try:
-        for S, T in ((0, 0), (0, 1), (8, 0), (1, 8), (8, 64), (3, 12), (64, 1000), (100000, 0)):
+        # (16, 160): the large-box default; (16, 128), (24, 200): medium cells of
+        # 97-160 particles on their own bitmask and list paths, larger ones on
+        # the shared-memory union-find
+        for S, T in ((0, 0), (0, 1), (8, 0), (1, 8), (8, 64), (3, 12), (64, 1000), (100000, 0), (16, 160),
+                     (16, 128), (24, 200), (16, -1)):
             J.set_cell_classes(S, T)
             _, r, H = run_fof(J, pos_np, spec.L, spec.b, spec.min_size)
             assert np.array_equal(r.label.cpu().numpy(), lab_ref), (S, T)
