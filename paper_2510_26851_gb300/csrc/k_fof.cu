@@ -269,12 +269,17 @@ __device__ __forceinline__ void lunite(int *lp, int a, int b) {
 
 // ---------------------------------------------------------------------------
 // Components of a cell of at most 32 R particles (staged in sp): lane owns
-// particles lane + 32 h (h < R) and their adjacency masks of R 32-bit words
-// (word indices are compile-time constants, so the masks stay in registers);
-// every pair is tested with the exact predicate.  Components by breadth-first
-// search from the lowest unvisited particle: a frontier step is one warp
-// OR-reduction per word, and the seed is the component's smallest local
-// index.  Writes parent[a0 + i] = a0 + seed of i's component.
+// particles lane + 32 h (h < R) and one adjacency row of R 32-bit words each
+// (word indices are compile-time constants, so the rows stay in registers).
+// Every unordered pair is tested once, with the exact predicate, and recorded
+// in one of its two rows: inside a word block, lane L tests the particles
+// L+1 .. L+16 of the block (indices mod 32); between blocks, the particle of
+// the higher block tests all of the lower block.  Components by breadth-first
+// search from the lowest unvisited particle: the neighbours of a frontier are
+// the bits of the frontier's rows (one warp OR-reduction per word) and the
+// particles whose own rows meet the frontier (one ballot per word); the seed
+// is the component's smallest local index.  Writes parent[a0 + i] = a0 + seed
+// of i's component.
 template <int R, bool NEAR>
 __device__ __forceinline__ void local_bitmask(const float4 *sp, int mA, uint32_t a0, int lane, const LinkGeom &g,
                                               int *parent) {
@@ -286,18 +291,22 @@ __device__ __forceinline__ void local_bitmask(const float4 *sp, int mA, uint32_t
         hv[h] = lane + 32 * h < mA;
         q[h] = hv[h] ? sp[lane + 32 * h] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int wd = 0; wd < R; ++wd) r[h][wd] = (hv[h] && wd == h) ? 1u << lane : 0u;
+        for (int wd = 0; wd < R; ++wd) r[h][wd] = 0u;
     }
 #pragma unroll
-    for (int wi = 0; wi < R; ++wi) {
-        const int iend = min(mA, 32 * wi + 32);
-        for (int i = 32 * wi; i < iend; ++i) {
-            const float4 pi = sp[i];
-            const uint32_t bi = 1u << (i & 31);
-#pragma unroll
-            for (int h = 0; h < R; ++h)
-                if (hv[h] && linked_if(NEAR, pi, q[h], g)) r[h][wi] |= bi;
+    for (int h = 0; h < R; ++h) {
+        // inside block h: the 16 particles after this lane's (cyclically)
+#pragma unroll 4
+        for (int d = 1; d <= 16; ++d) {
+            const int jl = (lane + d) & 31, j = 32 * h + jl;
+            if (hv[h] && j < mA && linked_if(NEAR, sp[j], q[h], g)) r[h][h] |= 1u << jl;
         }
+        // lower blocks: every particle
+#pragma unroll
+        for (int wi = 0; wi < h; ++wi)
+#pragma unroll 4
+            for (int i = 32 * wi; i < 32 * wi + 32; ++i)
+                if (hv[h] && linked_if(NEAR, sp[i], q[h], g)) r[h][wi] |= 1u << (i & 31);
     }
     uint32_t unv[R];
     int root[R];
@@ -336,6 +345,13 @@ __device__ __forceinline__ void local_bitmask(const float4 *sp, int mA, uint32_t
                 nb[wd] = __reduce_or_sync(0xffffffffu, v);
             }
 #pragma unroll
+            for (int h = 0; h < R; ++h) {
+                uint32_t meet = 0u;
+#pragma unroll
+                for (int wd = 0; wd < R; ++wd) meet |= r[h][wd] & fr[wd];
+                nb[h] |= __ballot_sync(0xffffffffu, meet != 0u);
+            }
+#pragma unroll
             for (int wd = 0; wd < R; ++wd) {
                 fr[wd] = nb[wd] & ~comp[wd];
                 comp[wd] |= nb[wd];
@@ -354,8 +370,8 @@ __device__ __forceinline__ void local_bitmask(const float4 *sp, int mA, uint32_t
 
 // Medium cells, local part: one warp per cell.  The cell's particles are
 // staged in shared memory and all their pairs tested (lane = one particle,
-// the other broadcast).  Up to kMedBig particles: adjacency bitmasks and a
-// breadth-first search over them; larger cells: a shared-memory union-find
+// the other broadcast).  Up to kMedBig particles: adjacency bitmasks, every
+// pair tested once, and a breadth-first search over them; larger cells: a shared-memory union-find
 // over local indices.  Then parent[slot] = first slot of the slot's local
 // component.  A cell larger than the staging area (possible only when it
 // cannot take the dense path) links its own pairs through the global forest
@@ -399,65 +415,12 @@ __global__ void __launch_bounds__(32 * W) medium_local_kernel(const float4 *__re
         }
         __syncwarp();
         if (!LARGE && mA <= 32) {
-            // One particle per lane: its 32-bit adjacency mask (every pair
-            // tested with the exact predicate).  Components by breadth-first
-            // search from the lowest unvisited particle: a frontier step is one
-            // warp OR-reduction of the frontier's rows, and the seed is the
-            // component's smallest local index.
-            const bool h0 = lane < mA;
-            float4 q0 = h0 ? sp[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-            unsigned r0 = h0 ? 1u << lane : 0u;
-            for (int i = 0; i < mA; ++i)
-                if (h0 && linked_if(NEAR, sp[i], q0, g)) r0 |= 1u << i;
-            unsigned unvisited = mA == 32 ? 0xffffffffu : (1u << mA) - 1u;
-            int root = 0;
-            while (unvisited) {
-                const int seed = __ffs(int(unvisited)) - 1;
-                unsigned comp = 1u << seed, frontier = comp;
-                while (frontier) {
-                    unsigned nb = __reduce_or_sync(0xffffffffu, ((frontier >> lane) & 1u) ? r0 : 0u);
-                    frontier = nb & ~comp;
-                    comp |= nb;
-                }
-                if ((comp >> lane) & 1u) root = seed;
-                unvisited &= ~comp;
-            }
-            if (h0) parent[a0 + lane] = int(a0) + root;
+            local_bitmask<1, NEAR>(sp, mA, a0, lane, g, parent);
             __syncwarp();
             continue;
         }
         if (!LARGE && mA <= 64) {
-            // The same for up to 64 particles: each lane owns particles lane
-            // and lane+32 and their 64-bit adjacency masks.
-            const bool h0 = lane < mA, h1 = lane + 32 < mA;
-            float4 q0 = h0 ? sp[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-            float4 q1 = h1 ? sp[lane + 32] : make_float4(0.f, 0.f, 0.f, 0.f);
-            unsigned long long r0 = h0 ? 1ull << lane : 0ull, r1 = h1 ? 1ull << (lane + 32) : 0ull;
-            for (int i = 0; i < mA; ++i) {
-                float4 pi = sp[i];
-                if (h0 && linked_if(NEAR, pi, q0, g)) r0 |= 1ull << i;
-                if (h1 && linked_if(NEAR, pi, q1, g)) r1 |= 1ull << i;
-            }
-            unsigned long long unvisited = mA == 64 ? ~0ull : (1ull << mA) - 1ull;
-            int root0 = 0, root1 = 0;
-            while (unvisited) {
-                const int seed = __ffsll((long long)unvisited) - 1;
-                unsigned long long comp = 1ull << seed, frontier = comp;
-                while (frontier) {
-                    unsigned long long v = (((frontier >> lane) & 1ull) ? r0 : 0ull) |
-                                           (((frontier >> (lane + 32)) & 1ull) ? r1 : 0ull);
-                    unsigned lo = __reduce_or_sync(0xffffffffu, unsigned(v));
-                    unsigned hi = __reduce_or_sync(0xffffffffu, unsigned(v >> 32));
-                    unsigned long long nb = (static_cast<unsigned long long>(hi) << 32) | lo;
-                    frontier = nb & ~comp;
-                    comp |= nb;
-                }
-                if ((comp >> lane) & 1ull) root0 = seed;
-                if ((comp >> (lane + 32)) & 1ull) root1 = seed;
-                unvisited &= ~comp;
-            }
-            if (h0) parent[a0 + lane] = int(a0) + root0;
-            if (h1) parent[a0 + lane + 32] = int(a0) + root1;
+            local_bitmask<2, NEAR>(sp, mA, a0, lane, g, parent);
             __syncwarp();
             continue;
         }
