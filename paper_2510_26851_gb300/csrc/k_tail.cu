@@ -14,7 +14,10 @@
 //            (orig, code) record per particle partitioned into buckets of
 //            2^shift consecutive original indices
 //   scatter  the records bucket after bucket into label[] and halo_id[]:
-//            the writes in flight cover one bucket, which stays in L2
+//            the writes in flight cover one bucket, which stays in L2.  A
+//            particle alone in its component and not a halo (about 46% of
+//            them in the clustered boxes) gets no record: label[] is first
+//            filled with the own index and halo_id[] with -1
 // The members of each halo are then sorted ascending (segmented sort).
 #include "jfof_internal.cuh"
 #include "k_fof.cuh"
@@ -23,6 +26,9 @@
 namespace jfof {
 
 constexpr int kTailThreads = 256;
+// Code of a root whose component is the particle alone (and not a halo): it
+// gets no record; its label (its own index) and halo id (-1) are pre-filled.
+constexpr int32_t kSingleton = -2;
 constexpr int kTailItems = 16;
 constexpr int kTailTile = kTailThreads * kTailItems;
 constexpr int kTailBPT = kTailBuckets / kTailThreads;  // bucket counters per thread
@@ -96,7 +102,7 @@ __global__ void __launch_bounds__(256) tail_codes_kernel(const int *__restrict__
     for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < N; s += int64_t(gridDim.x) * blockDim.x) {
         if (parent[s] != int(s)) continue;
         uint32_t n = rsize[s];
-        int32_t code = -1;
+        int32_t code = n == 1u ? kSingleton : -1;
         if (n >= min_size) {
             int l = rootmin[s];
             uint32_t h = prefix[l >> 5] + uint32_t(__popc(bits[l >> 5] & ((1u << (l & 31)) - 1u)));
@@ -112,7 +118,8 @@ __global__ void __launch_bounds__(256) tail_codes_kernel(const int *__restrict__
 template <bool GROUPS>
 __global__ void __launch_bounds__(kTailThreads) tail_partition_kernel(
     const float4 *__restrict__ spos, int64_t N, const int *__restrict__ parent, const int *__restrict__ rootmin,
-    const int32_t *__restrict__ code_of, uint32_t *__restrict__ cursor, int32_t *__restrict__ members,
+    const int32_t *__restrict__ code_of, const uint32_t *__restrict__ size_of, uint32_t *__restrict__ cursor,
+    int32_t *__restrict__ members,
     uint32_t *__restrict__ bucket_fill, int shift, uint2 *__restrict__ rec) {
     __shared__ uint32_t hist[kTailBuckets], lstart[kTailBuckets], gbase[kTailBuckets];
     __shared__ uint32_t warp_sums[kTailThreads / 32];
@@ -130,11 +137,17 @@ __global__ void __launch_bounds__(kTailThreads) tail_partition_kernel(
         int orig = 0;
         int32_t code = -1;
         uint32_t y = 0u;
+        bool single = false;
         if (ok) {
             int r = parent[s];
             orig = __float_as_int(spos[s].w);
-            if (GROUPS) code = code_of[r];
-            y = code >= 0 ? (0x80000000u | uint32_t(code)) : uint32_t(rootmin[r]);
+            if (GROUPS) {
+                code = code_of[r];
+                single = code == kSingleton;
+            } else {
+                single = size_of[r] == 1u;
+            }
+            if (!single) y = code >= 0 ? (0x80000000u | uint32_t(code)) : uint32_t(rootmin[r]);
         }
         if (GROUPS) {
             // a warp's 32 consecutive slots: one cursor bump per halo present
@@ -148,9 +161,10 @@ __global__ void __launch_bounds__(kTailThreads) tail_partition_kernel(
                 members[b + uint32_t(__popc(grp & ((1u << lane) - 1u)))] = orig;
             }
         }
-        key[k] = ok ? uint32_t(orig) : 0xffffffffu;
+        const bool rec_ok = ok && !single;  // a singleton's outputs are pre-filled
+        key[k] = rec_ok ? uint32_t(orig) : 0xffffffffu;
         val[k] = y;
-        rank[k] = ok ? atomicAdd(&hist[uint32_t(orig) >> shift], 1u) : 0u;
+        rank[k] = rec_ok ? atomicAdd(&hist[uint32_t(orig) >> shift], 1u) : 0u;
     }
     __syncthreads();
     uint32_t c[kTailBPT], sum = 0u, total;
@@ -180,13 +194,17 @@ __global__ void __launch_bounds__(kTailThreads) tail_partition_kernel(
     }
 }
 
+// Records of bucket b sit at [b << shift, (b << shift) + fill[b]); labels and
+// halo ids not written here were pre-filled (own index, -1).
 template <bool GROUPS>
 __global__ void __launch_bounds__(256) tail_scatter_kernel(const uint2 *__restrict__ rec, int64_t N,
+                                                           const uint32_t *__restrict__ fill, int shift,
                                                            const int32_t *__restrict__ hlabel,
                                                            int32_t *__restrict__ label,
                                                            int32_t *__restrict__ halo_id) {
     int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (e >= N) return;
+    if (uint32_t(e - ((e >> shift) << shift)) >= fill[e >> shift]) return;
     uint2 r = rec[e];
     if (GROUPS && (r.y & 0x80000000u)) {
         int32_t h = int32_t(r.y & 0x7fffffffu);
@@ -194,8 +212,12 @@ __global__ void __launch_bounds__(256) tail_scatter_kernel(const uint2 *__restri
         halo_id[r.x] = h;
     } else {
         label[r.x] = int32_t(r.y);
-        if (GROUPS) halo_id[r.x] = -1;
     }
+}
+
+__global__ void __launch_bounds__(256) iota_fill_kernel(int32_t *__restrict__ p, int64_t N) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x)
+        p[i] = int32_t(i);
 }
 
 static void tail_roots(const FofBuffers &fb, const TailView &v, int64_t N, cudaStream_t s) {
@@ -213,9 +235,11 @@ void launch_tail_labels(const FofBuffers &fb, int64_t N, int32_t *label, cudaStr
     int shift = bucket_shift(N);
     {
         JFOF_TRACE("finalize_labels", s);
+        iota_fill_kernel<<<grid_for(N, 256), 256, 0, s>>>(label, N);
         tail_partition_kernel<false><<<unsigned((N + kTailTile - 1) / kTailTile), kTailThreads, 0, s>>>(
-            fb.spos, N, fb.parent, v.rootmin, nullptr, nullptr, nullptr, fb.bucket_fill, shift, v.rec);
-        tail_scatter_kernel<false><<<grid_full(N, 256), 256, 0, s>>>(v.rec, N, nullptr, label, nullptr);
+            fb.spos, N, fb.parent, v.rootmin, nullptr, v.rsize, nullptr, nullptr, fb.bucket_fill, shift, v.rec);
+        tail_scatter_kernel<false><<<grid_full(N, 256), 256, 0, s>>>(v.rec, N, fb.bucket_fill, shift, nullptr, label,
+                                                                      nullptr);
     }
 }
 
@@ -246,12 +270,15 @@ void launch_tail_groups(const FofBuffers &fb, int64_t N, int32_t min_size, int64
     {
         JFOF_TRACE("members_fill", s);
         tail_partition_kernel<true><<<unsigned((N + kTailTile - 1) / kTailTile), kTailThreads, 0, s>>>(
-            fb.spos, N, fb.parent, v.rootmin, reinterpret_cast<const int32_t *>(v.rsize), gb.cursor, members,
-            fb.bucket_fill, shift, v.rec);
+            fb.spos, N, fb.parent, v.rootmin, reinterpret_cast<const int32_t *>(v.rsize), nullptr, gb.cursor,
+            members, fb.bucket_fill, shift, v.rec);
     }
     {
         JFOF_TRACE("finalize_labels", s);
-        tail_scatter_kernel<true><<<grid_full(N, 256), 256, 0, s>>>(v.rec, N, gb.hlabel, label, halo_id);
+        iota_fill_kernel<<<grid_for(N, 256), 256, 0, s>>>(label, N);
+        cudaMemsetAsync(halo_id, 0xff, sizeof(int32_t) * size_t(N), s);
+        tail_scatter_kernel<true><<<grid_full(N, 256), 256, 0, s>>>(v.rec, N, fb.bucket_fill, shift, gb.hlabel, label,
+                                                                     halo_id);
     }
     launch_segsort(reinterpret_cast<const uint32_t *>(halo_start), H_cap, members, N, s, n_halos, gb.seglist,
                    gb.seglist_words);
