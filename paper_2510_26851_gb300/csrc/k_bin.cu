@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(kFewThreads) bin_scatter_few_kernel(const floa
 // work list.
 constexpr int kSortThreads = 512;
 constexpr int kSortUnroll = 2;
+constexpr int kSmallStage = 4096;  // small-cell slots of a brick staged in shared memory (at most)
 
 // Cell of a particle inside its brick (0..4095).
 __device__ __forceinline__ uint32_t local_cell(float4 q, const BinGeom &g) {
@@ -171,6 +172,7 @@ __global__ void __launch_bounds__(kSortThreads) brick_sort_kernel(const float4 *
                                                                   float4 *__restrict__ spos,
                                                                   uint32_t *__restrict__ cell_start, ClassReg cr) {
     __shared__ uint32_t hist[kBrickCells];
+    __shared__ uint32_t stage[kSmallStage];  // the brick's small-cell slots, in order
     __shared__ uint32_t warps[kSortThreads / 32];
     __shared__ uint32_t small_base;
     constexpr int per = kBrickCells / kSortThreads;  // 8
@@ -240,12 +242,26 @@ __global__ void __launch_bounds__(kSortThreads) brick_sort_kernel(const float4 *
             uint32_t so = block_exclusive_scan(ns, warps, &ntot);
             if (threadIdx.x == 0) small_base = ntot ? atomicAdd(cr.nsmall, ntot) : 0u;
             __syncthreads();
-            uint32_t w = small_base + so, cs = bs + pre - s;  // pre has advanced past this thread's cells
+            uint32_t cs = bs + pre - s;  // pre has advanced past this thread's cells
+            if (ntot <= uint32_t(kSmallStage)) {
+                // through shared memory, so the list leaves in coalesced runs
+                uint32_t w = so;
 #pragma unroll
-            for (int k = 0; k < per; ++k) {
-                if (v[k] <= uint32_t(cr.S))
-                    for (uint32_t q = 0; q < v[k]; ++q) cr.small_slots[w++] = cs + q;
-                cs += v[k];
+                for (int k = 0; k < per; ++k) {
+                    if (v[k] <= uint32_t(cr.S))
+                        for (uint32_t q = 0; q < v[k]; ++q) stage[w++] = cs + q;
+                    cs += v[k];
+                }
+                __syncthreads();
+                for (uint32_t i = threadIdx.x; i < ntot; i += kSortThreads) cr.small_slots[small_base + i] = stage[i];
+            } else {
+                uint32_t w = small_base + so;
+#pragma unroll
+                for (int k = 0; k < per; ++k) {
+                    if (v[k] <= uint32_t(cr.S))
+                        for (uint32_t q = 0; q < v[k]; ++q) cr.small_slots[w++] = cs + q;
+                    cs += v[k];
+                }
             }
         }
         __syncthreads();
