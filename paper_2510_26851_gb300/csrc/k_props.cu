@@ -137,35 +137,32 @@ __global__ void __launch_bounds__(256) halo_props_kernel(const float *__restrict
         KSum sx[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         KSum sv[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         Moments mv{0.f, {0.f, 0.f, 0.f}, 0.f};
-        for (int k0 = hs + lane; k0 < he; k0 += 64) {
-            // two members per lane per step: all six gathers issue before the sums
-            int k1 = k0 + 32;
-            bool two = k1 < he;
-            int i0 = members[k0];
-            int i1 = two ? members[k1] : i0;
-            float p0[3], p1[3], v0[3] = {0.f, 0.f, 0.f}, v1[3] = {0.f, 0.f, 0.f};
+        constexpr int U = 4;  // members per lane per step: all gathers issue before the sums
+        for (int k0 = hs + lane; k0 < he; k0 += 32 * U) {
+            int idx[U];
+            bool on[U];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                p0[a] = load_coord(pos, i0, a, L, wrap);
-                p1[a] = load_coord(pos, i1, a, L, wrap);
-                if (vel) {
-                    v0[a] = vel[3 * int64_t(i0) + a];
-                    v1[a] = vel[3 * int64_t(i1) + a];
-                }
+            for (int u = 0; u < U; ++u) {
+                on[u] = k0 + 32 * u < he;
+                idx[u] = on[u] ? members[k0 + 32 * u] : members[k0];
             }
+            float pp[U][3], vv[U][3];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                kadd(sx[a], min_image(p0[a], xr[a], L, hL));
-                if (vel) kadd(sv[a], __fsub_rn(v0[a], vr[a]));
-            }
-            if (vel) welford(mv, v0);
-            if (two) {
+            for (int u = 0; u < U; ++u)
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    kadd(sx[a], min_image(p1[a], xr[a], L, hL));
-                    if (vel) kadd(sv[a], __fsub_rn(v1[a], vr[a]));
+                    pp[u][a] = load_coord(pos, idx[u], a, L, wrap);
+                    vv[u][a] = vel ? vel[3 * int64_t(idx[u]) + a] : 0.f;
                 }
-                if (vel) welford(mv, v1);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (!on[u]) continue;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    kadd(sx[a], min_image(pp[u][a], xr[a], L, hL));
+                    if (vel) kadd(sv[a], __fsub_rn(vv[u][a], vr[a]));
+                }
+                if (vel) welford(mv, vv[u]);
             }
         }
         float vm[3];
