@@ -38,7 +38,7 @@ namespace {
 
 struct TailView {
     int *rootmin;     // [N] smallest original index of the root's component
-    uint32_t *rsize;  // [N] component size at the root; then its halo id or -1
+    uint32_t *rsize;  // [N] component size at the root; then its halo id, -1 or kSingleton
     uint2 *rec;       // [N] (orig, code) grouped by bucket of orig
 };
 
@@ -115,6 +115,8 @@ __global__ void __launch_bounds__(256) tail_codes_kernel(const int *__restrict__
     if (blockIdx.x == 0 && threadIdx.x == 0) *n_halos = int32_t(prefix[W]);
 }
 
+// Per root, GROUPS reads its code (halo id, -1, or kSingleton) from code_of;
+// the labels-only form reads its component size from size_of (1: singleton).
 template <bool GROUPS>
 __global__ void __launch_bounds__(kTailThreads) tail_partition_kernel(
     const float4 *__restrict__ spos, int64_t N, const int *__restrict__ parent, const int *__restrict__ rootmin,
